@@ -1,0 +1,207 @@
+/*
+ * heataco.h -- C ABI of the GB300 (sm_103a) HeatACO decoder.
+ *
+ * HeatACO (arXiv 2601.19041) decodes a fixed edge-confidence heatmap H into a
+ * TSP / ATSP tour with a Max-Min Ant System whose construction weight is
+ * tau^alpha * eta^beta * e^kappa (Sec. III-A, eq. transition).  The decoding
+ * problem it solves is g(H, D) -> tour (Sec. II-B): distances (coordinates or
+ * a cost matrix) and a sparse heatmap in, a feasible tour and its length out,
+ * following Algorithm 1 (the MMAS loop) and Algorithm 2 (one ant's tour).
+ *
+ * Conventions used by every entry point:
+ *   - All functions return an int status: HAC_OK (0) or a negative HAC_E* code.
+ *     No function aborts, throws or exits; hac_strerror() names a code.
+ *   - The library never allocates device memory.  The caller passes a device
+ *     workspace of at least the size reported by the matching *_workspace_size
+ *     call (any allocator: cudaMalloc, a PyTorch tensor, a pool).  The
+ *     workspace must stay valid, and must not be used by anyone else, until
+ *     the handle that was created on it is destroyed.  The library keeps host
+ *     memory for its handles only.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     device work of a handle is issued on the stream given at its creation.
+ *   - Input pointers are host pointers unless `inputs_on_device` is 1, in which
+ *     case they are device pointers that must stay valid and unchanged until
+ *     the handle is destroyed.  Outputs are caller-owned host buffers.
+ *   - Tours are permutations of 0..n-1 in visiting order, in the orientation
+ *     and rotation the search produced them.  Lengths are FP64 (eq. tour_length).
+ *   - Results are a deterministic function of the inputs and parameters: the
+ *     random numbers come from a counter-based Philox4x32-10 keyed by the
+ *     instance's seed and (iteration, ant, step), so an instance decodes to the
+ *     same tour alone, in any batch and in any serving mix.
+ */
+#ifndef HEATACO_H
+#define HEATACO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum hac_status {
+    HAC_OK = 0,
+    HAC_EINVAL = -1,        /* invalid argument or malformed instance */
+    HAC_ENOMEM = -2,        /* workspace too small, or host allocation failed */
+    HAC_ECUDA = -3,         /* a CUDA runtime call failed (see hac_last_cuda_error) */
+    HAC_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+    HAC_EUNSUPPORTED = -5,  /* combination not supported (e.g. 2-opt on an ATSP) */
+    HAC_EBUSY = -6          /* serving: request not finished yet / no slot free */
+};
+
+#define HAC_KMAX 32         /* candidate-list size limit (one 8-lane warp segment) */
+#define HAC_NMAX (1 << 20)  /* node-count limit of one instance */
+
+/* One decode problem (Sec. II-A, II-B).
+ *   kind 0: symmetric Euclidean; d_ij = sqrt((x_j-x_i)^2 + (y_j-y_i)^2) in FP64
+ *           of the FP32 coordinates `coords` (n*2, x0 y0 x1 y1 ...).
+ *   kind 1: explicit costs `cost` (n*n FP32 row-major, c_ij = cost[i*n+j]);
+ *           directed (ATSP): the pheromone deposit is one-directional.
+ * The heatmap H (eq. heatmap_def) is CSR: h_rowptr (n+1 int32, h_rowptr[0]=0),
+ * h_col (nnz int32, strictly increasing within a row, no i==j), h_val (nnz
+ * values in [0,1], FP32 when h_dtype==0, IEEE binary16 when h_dtype==1).
+ * symmetrize=1 makes the decoder use (H + H^T)/2 (Sec. II-B). */
+typedef struct {
+    int32_t n;
+    int32_t kind;
+    const float *coords;
+    const float *cost;
+    const int32_t *h_rowptr;
+    const int32_t *h_col;
+    const void *h_val;
+    int32_t h_dtype;
+    int32_t symmetrize;
+} hac_instance;
+
+/* Decoder parameters (Sec. IV-D).  hac_params_default() fills the paper's
+ * values: m=32, k=20, I=5000, alpha=1, beta=2, rho=0.8 (0.2 for kind 1),
+ * theta_h=1e-4, eps=1e-9, c_cap=0.5, q_level=0.90, p_best=0.05, d*=2 (1 for
+ * kind 1), no local search, baseline over C_i, ls_k=20.
+ *   logw_clip       cap of the log-weight kappa*ln(e) (end of Sec. III-C; the
+ *                   paper says "a large constant"; default 30).
+ *   local_search    0 none; 1 first-improvement 2-opt with geometric
+ *                   neighbour lists and don't-look bits (Sec. III-D) on the
+ *                   iteration-best tour and on T_NN; tau_min = tau_max/(2n).
+ *   baseline_scope  0: order statistic b_i over the candidates C_i; 1: over all
+ *                   heatmap entries of row i (eq. background).
+ *   seed            key of the instance's Philox stream. */
+typedef struct {
+    int32_t m, k, iterations;
+    double alpha, beta, rho;
+    double theta_h, eps, c_cap, q_level, p_best, logw_clip;
+    int32_t degree_target;
+    int32_t local_search;
+    int32_t baseline_scope;
+    int32_t ls_k;
+    uint64_t seed;
+} hac_params;
+
+/* Execution options of a batch (none of them changes any result). */
+typedef struct {
+    int32_t ants_per_warp;    /* 1, 2 or 4 ants share one warp (8-lane segments); 0 = auto */
+    int32_t warps_per_block;  /* construction block size in warps; 0 = auto */
+    int32_t use_graph;        /* 1: capture the iteration loop in a CUDA graph */
+    int32_t fused;            /* 1: persistent fused construct+update kernel; 0: per-step launches */
+    int32_t fallback_list;    /* nearest-unvisited lookup list length (0, 8, 16, 32); 0 = scan only */
+} hac_exec;
+
+int hac_params_default(hac_params *p, int32_t kind);
+int hac_exec_default(hac_exec *e);
+const char *hac_strerror(int status);
+/* The last CUDA error seen by the calling thread (cudaError_t as int, 0 if none). */
+int hac_last_cuda_error(void);
+int hac_version(void);
+
+/* ------------------------------------------------------------------ batches
+ * A batch is `count` independent instances decoded together on one GPU: each
+ * instance has its own parameters (m, k, iterations, seed, ...), pheromone and
+ * best-tour state, all resident in the workspace.  Algorithm 1 lines 1-6
+ * (preparation: candidate lists of Sec. III-A, evidence and kappa of
+ * Sec. III-C, T_NN and the bounds of eq. tau_init / tau_min_nols) run in
+ * hac_batch_create; lines 8-21 (construction by Algorithm 2, iteration best,
+ * global best with recomputed bounds, bounded evaporation/deposit of eq.
+ * pheromone_update) run in hac_batch_iterate. */
+typedef struct hac_batch hac_batch;
+
+/* Bytes of device workspace needed by hac_batch_create for these instances.
+ * Validates sizes and parameters (not the heatmap contents).  Host-only,
+ * except that with inputs_on_device==1 it reads h_rowptr[n] of each instance
+ * from the device (a synchronous 4-byte copy). */
+int hac_batch_workspace_size(const hac_instance *ins, const hac_params *ps, int32_t count,
+                             int32_t inputs_on_device, size_t *bytes);
+
+/* Creates the handle, copies the inputs into the workspace (host->device
+ * copies when inputs_on_device==0), validates the heatmap on the device and
+ * enqueues the preparation.  Asynchronous on `stream`; errors found by the
+ * device validation are reported by the next synchronising call.
+ * exec may be NULL (defaults).  On failure *out is NULL. */
+int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t count,
+                     int32_t inputs_on_device, void *workspace, size_t ws_bytes,
+                     const hac_exec *exec, void *stream, hac_batch **out);
+
+/* Enqueues `iters` more iterations of every instance that has not reached its
+ * own iteration budget (instances stop at their budget).  Asynchronous. */
+int hac_batch_iterate(hac_batch *bt, int32_t iters);
+
+/* Enqueues all remaining iterations.  Asynchronous. */
+int hac_batch_run(hac_batch *bt);
+
+/* Synchronises the stream and reports the first device-side error (bad
+ * heatmap, timeout) as a status. */
+int hac_batch_sync(hac_batch *bt);
+
+/* Fields readable with hac_batch_read (sizes in elements):
+ *   CAND   int32  n*k_pad   candidate list C_i, -1 on padding, ascending (d, j)
+ *   CDIST  f64    n*k_pad   d_ij of each candidate slot
+ *   CONF   f64    n*k_pad   thresholded confidence c_ij (eq. confidence)
+ *   BASE   f64    n         degree baseline b_i (eq. background)
+ *   EVID   f64    n*k_pad   evidence factor e_ij (eq. evidence)
+ *   W      f32    n*k_pad   static weight fl32(eta^beta * e^kappa)
+ *   TAU    f32    n*k_pad   pheromone
+ *   CHOICE f32    n*k_pad   fl32(tau^alpha * W), the numerator of eq. transition
+ *   NN_TOUR int32 n         T_NN
+ *   GB_TOUR int32 n         T_gb
+ *   IB_TOUR int32 n         last iteration-best tour (after local search)
+ *   TOURS  int32  m*n       the m tours of the last iteration
+ *   LENS   f64    m         their lengths
+ *   SCALARS f64   16        q90, Rhat, kappa, p_x, L_nn, tau_max64, tau_min64,
+ *                           tau_max, tau_min, L_gb, L_ib, n_lambda, t, ib_ant,
+ *                           n_fallback, k_pad
+ *   NBR    int32  n*ls_k    geometric 2-opt neighbour lists
+ *   TRACE  f64    3*I       per iteration: ib ant, L_ib, L_gb
+ * The call synchronises the stream. */
+enum hac_field {
+    HAC_F_CAND = 1, HAC_F_CDIST, HAC_F_CONF, HAC_F_BASE, HAC_F_EVID, HAC_F_W, HAC_F_TAU,
+    HAC_F_CHOICE, HAC_F_NN_TOUR, HAC_F_GB_TOUR, HAC_F_IB_TOUR, HAC_F_TOURS, HAC_F_LENS,
+    HAC_F_SCALARS, HAC_F_NBR, HAC_F_TRACE
+};
+int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size_t bytes);
+
+/* Copies every instance's best tour T_gb (best_tours[b]: n_b int32) and length
+ * L_gb (best_lens[b]) to host buffers; synchronises.  Either array may be NULL. */
+int hac_batch_results(hac_batch *bt, int32_t *const *best_tours, double *best_lens);
+
+/* Total ant-steps (sum of m*n*iterations done) and fallback steps so far. */
+int hac_batch_counters(hac_batch *bt, int64_t *ant_steps, int64_t *fallback_steps);
+
+/* Releases the host handle; the workspace can be reused afterwards.  Does not
+ * synchronise: the caller must not reuse the workspace before the stream has
+ * drained. */
+int hac_batch_destroy(hac_batch *bt);
+
+/* ------------------------------------------------------------------ one-shot
+ * Decode one instance / a batch end to end (create, run, results, destroy) and
+ * synchronise.  statuses (count entries, may be NULL) receives per-instance
+ * status. */
+int hac_solve(const hac_instance *in, const hac_params *p, int32_t inputs_on_device,
+              void *workspace, size_t ws_bytes, int32_t *best_tour, double *best_len,
+              void *stream);
+int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count,
+                    int32_t inputs_on_device, void *workspace, size_t ws_bytes,
+                    const hac_exec *exec, int32_t *const *best_tours, double *best_lens,
+                    int32_t *statuses, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEATACO_H */

@@ -477,7 +477,9 @@ static void apply_2opt_succ(int32_t *tour, int32_t *pos, int n, int a, int b)
  * A reversal flips succ/pred inside the reversed range, which can open moves
  * at cities whose bits are set, so the passes run in rounds that start with
  * all bits clear; the search ends after a round whose first pass (over every
- * city) makes no move, i.e. at a local optimum of the neighbour-list moves. */
+ * city) makes no move, i.e. at a local optimum of the neighbour-list moves.
+ * A call stops after 64n + 1024 moves, a guard that strictly decreasing tour
+ * lengths never reach in practice. */
 int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour)
 {
     int n = in->n;
@@ -486,13 +488,14 @@ int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour
     if (!pos || !dlb) { free(pos); free(dlb); return ORC_ENOMEM; }
     for (int p = 0; p < n; ++p) pos[tour[p]] = p;
     int moves = 0, round_moves;
+    const long long max_moves = 64LL * n + 1024;
     do {
       round_moves = 0;
       memset(dlb, 0, (size_t)n);
       int improved = 1;
-      while (improved) {
+      while (improved && moves < max_moves) {
         improved = 0;
-        for (int p = 0; p < n; ++p) {
+        for (int p = 0; p < n && moves < max_moves; ++p) {
             int a = tour[p];
             if (dlb[a]) continue;
             int moved;
@@ -517,11 +520,11 @@ int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour
                         }
                     }
                 }
-            } while (moved);
+            } while (moved && moves < max_moves);
             dlb[a] = 1;
         }
       }
-    } while (round_moves > 0);
+    } while (round_moves > 0 && moves < max_moves);
     free(pos); free(dlb);
     return moves;
 }

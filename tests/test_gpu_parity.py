@@ -1,0 +1,194 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bar (both sides evaluate every FP step in the same fixed order): integer and
+index results bit-exact (candidate lists, tours, iteration-best ants);
+floating-point prep arrays, lengths and pheromone bit-exact as well, which
+is stricter than the 1e-6 relative pheromone tolerance the path promises.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from helpers import atsp, dmat, euclid, is_perm, params
+from paper_2601_19041_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TAU_RTOL = 1e-6      # stated pheromone tolerance; observed differences are 0
+
+
+@pytest.fixture(scope="module")
+def hac():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_19041_gb300 import build, heataco
+    build.build()
+    return heataco
+
+
+def prep_equal(bt, b, o):
+    for f, of in [("CAND", "cand"), ("CDIST", "cdist"), ("CONF", "conf"), ("BASE", "base"),
+                  ("EVID", "evid"), ("W", "W"), ("NN_TOUR", "nn_tour"), ("TAU", "tau"),
+                  ("CHOICE", "choice")]:
+        g, r = bt.read(b, f), o.get(of)
+        assert g.shape == r.shape, f
+        assert np.array_equal(g, r), f"{f}: {np.argwhere(g != r)[:5]}"
+    gs, os_ = bt.scalars(b), o.scalars()
+    for key in ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
+                "tau_min", "n_lambda"):
+        assert gs[key] == os_[key], key
+
+
+def search_equal(bt, b, o, iters):
+    tr = bt.read(b, "TRACE")
+    assert np.array_equal(tr[:iters, 0].astype(np.int64), o.get("trace_ib")[:iters]), "ib ants"
+    assert np.array_equal(tr[:iters, 1], o.get("trace_Lib")[:iters]), "L_ib"
+    assert np.array_equal(tr[:iters, 2], o.get("trace_Lgb")[:iters]), "L_gb"
+    if iters:
+        assert np.array_equal(bt.read(b, "TOURS"), o.get("tours")), "tours"
+        assert np.array_equal(bt.read(b, "LENS"), o.get("lens")), "lens"
+        assert np.array_equal(bt.read(b, "IB_TOUR"), o.get("ib_tour")), "ib tour"
+    gt, rt = bt.read(b, "TAU"), o.get("tau")
+    assert np.allclose(gt, rt, rtol=TAU_RTOL, atol=0)
+    assert np.array_equal(gt, rt), "tau bitwise"
+    assert np.array_equal(bt.read(b, "CHOICE"), o.get("choice")), "choice"
+    assert np.array_equal(bt.read(b, "GB_TOUR"), o.get("gb_tour")), "gb tour"
+    gs, os_ = bt.scalars(b), o.scalars()
+    assert gs["L_gb"] == os_["L_gb"]
+    assert int(gs["n_fallback"]) == o.ints()["n_fallback"]
+
+
+def run_case(hac, orc, insts, ps, iters=None, exec_=None):
+    bt = hac.Batch(insts, ps, exec_)
+    try:
+        bt.sync()
+        for b in range(len(insts)):
+            prep_equal(bt, b, orc.Oracle(insts[b], dataclasses.replace(ps[b])))
+        bt.run().sync()
+        for b in range(len(insts)):
+            o = orc.Oracle(insts[b], ps[b]).iterate(ps[b].iterations)
+            search_equal(bt, b, o, ps[b].iterations)
+        tours, lens = bt.results()
+        for b in range(len(insts)):
+            assert is_perm(tours[b], insts[b].n)
+    finally:
+        bt.close()
+
+
+def _pts(seed, n):
+    return np.random.default_rng(seed).random((n, 2)).astype(np.float32)
+
+
+CASES = {
+    "sym50nn_k20": lambda: (synth.euclid_instance(11, 300, K=50), params(m=20, k=20, iterations=12, rho=0.2, seed=5)),
+    "sym10nn_k10_ragged": lambda: (synth.euclid_instance(12, 257, K=10), params(m=13, k=10, iterations=10, rho=0.2, seed=6)),
+    "k32": lambda: (synth.euclid_instance(13, 150, K=40), params(m=9, k=32, iterations=8, rho=0.2, seed=7)),
+    "k7_pad": lambda: (synth.euclid_instance(14, 123, K=12), params(m=7, k=7, iterations=9, rho=0.8, seed=8)),
+    "n_le_k": lambda: (synth.euclid_instance(15, 6, K=3), params(m=5, k=20, iterations=6, rho=0.2, seed=9)),
+    "n3": lambda: (euclid(_pts(3, 3)), params(m=4, k=20, iterations=3, rho=0.2, seed=1)),
+    "empty_heatmap": lambda: (euclid(_pts(16, 140)), params(m=10, k=20, iterations=8, rho=0.2, seed=10)),
+    "dense_heatmap": lambda: (euclid(_pts(17, 70), np.where(np.eye(70) > 0, 0, np.random.default_rng(1).random((70, 70)))),
+                              params(m=8, k=20, iterations=6, rho=0.2, seed=11)),
+    "asym_no_symmetrize": lambda: (dataclasses.replace(synth.euclid_instance(18, 180, K=20), symmetrize=0),
+                                   params(m=10, k=12, iterations=7, rho=0.2, seed=12)),
+    "fp16_heatmap": lambda: (synth.euclid_instance(19, 222, K=50, dtype=np.float16), params(m=12, k=20, iterations=7, rho=0.2, seed=13)),
+    "baseline_row_scope": lambda: (synth.euclid_instance(20, 160, K=50), params(m=8, k=8, iterations=6, rho=0.2, seed=14, baseline_scope=1)),
+    "alpha_beta_powers": lambda: (synth.euclid_instance(21, 130, K=30), params(m=8, k=16, iterations=6, rho=0.3, seed=15, alpha=1.5, beta=3.0)),
+    "duplicate_points": lambda: (euclid(np.repeat(_pts(22, 40), 2, axis=0)), params(m=6, k=8, iterations=5, rho=0.2, seed=16)),
+    "atsp": lambda: (synth.atsp_instance(23, 200, K=30), params(m=10, k=20, iterations=8, rho=0.2, degree_target=1, seed=17)),
+    "two_opt": lambda: (synth.euclid_instance(24, 350, K=10), params(m=10, k=10, iterations=6, rho=0.2, local_search=1, seed=18)),
+    "clustered": lambda: (synth.euclid_instance(25, 300, K=50, family="gmm"), params(m=12, k=20, iterations=6, rho=0.2, seed=19)),
+    "grid": lambda: (synth.euclid_instance(26, 289, K=50, family="grid"), params(m=12, k=20, iterations=6, rho=0.2, seed=20)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_case_parity(hac, orc, name):
+    inst, p = CASES[name]()
+    run_case(hac, orc, [inst], [p])
+
+
+@pytest.mark.parametrize("apw,wpb,graph", [(1, 4, 1), (2, 8, 0), (4, 2, 1), (4, 8, 0)])
+def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph):
+    inst = synth.euclid_instance(31, 410, K=50)
+    p = params(m=21, k=20, iterations=23, rho=0.2, seed=3)
+    run_case(hac, orc, [inst], [p], exec_=hac.make_exec(apw, wpb, graph))
+
+
+def test_mixed_batch_parity(hac, orc):
+    insts, ps = [], []
+    for b, (n, k, m, kind, ls) in enumerate([(120, 20, 9, 0, 0), (333, 10, 17, 0, 1), (64, 8, 4, 1, 0),
+                                              (501, 20, 33, 0, 0), (7, 20, 3, 0, 0)]):
+        if kind == 1:
+            insts.append(synth.atsp_instance(40 + b, n, K=20))
+            ps.append(params(m=m, k=k, iterations=5 + b, rho=0.2, degree_target=1, seed=100 + b))
+        else:
+            insts.append(synth.euclid_instance(40 + b, n, K=20))
+            ps.append(params(m=m, k=k, iterations=5 + b, rho=0.2, local_search=ls, seed=100 + b))
+    run_case(hac, orc, insts, ps)
+
+
+def test_iterate_in_steps_equals_run(hac, orc):
+    inst = synth.euclid_instance(50, 200, K=50)
+    p = params(m=16, k=20, iterations=27, rho=0.2, seed=4)
+    with hac.Batch([inst], [p]) as bt:
+        for chunk in (1, 2, 10, 3, 11, 50):
+            bt.iterate(chunk)
+        bt.sync()
+        o = orc.Oracle(inst, p).iterate(27)
+        search_equal(bt, 0, o, 27)
+        assert bt.scalars(0)["t"] == 27
+
+
+def test_batch_membership_does_not_change_results(hac):
+    insts, ps = synth.workload("batch128", count=6)
+    for p in ps:
+        p.iterations = 15
+    _, lens_all = hac.solve_batch(insts, ps)
+    for b in (0, 3, 5):
+        t1, l1 = hac.solve(insts[b], ps[b])
+        assert l1 == lens_all[b]
+
+
+def test_full_size_tsp500(hac, orc):
+    insts, ps = synth.workload("tsp500")
+    run_case(hac, orc, insts, ps)
+
+
+def _oracle_many(orc, insts, ps):
+    import concurrent.futures as cf
+    def one(b):
+        return orc.Oracle(insts[b], ps[b]).iterate(ps[b].iterations)
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:   # the C oracle releases the GIL
+        return list(ex.map(one, range(len(insts))))
+
+
+@pytest.mark.parametrize("name,sample", [("batch128", (0, 37, 90, 127)), ("atsp1000", (0, 31, 63))])
+def test_full_size_workload_sampled(hac, orc, name, sample):
+    insts, ps = synth.workload(name)
+    bt = hac.Batch(insts, ps)
+    try:
+        bt.run().sync()
+        sub_i = [insts[b] for b in sample]
+        sub_p = [ps[b] for b in sample]
+        oracles = _oracle_many(orc, sub_i, sub_p)
+        for b, o in zip(sample, oracles):
+            search_equal(bt, b, o, ps[b].iterations)
+    finally:
+        bt.close()
+
+
+def test_full_size_tsp10k_two_opt_sampled(hac, orc):
+    insts, ps = synth.workload("tsp10k_2opt")
+    bt = hac.Batch(insts, ps)
+    try:
+        bt.run().sync()
+        o = _oracle_many(orc, [insts[5]], [ps[5]])[0]
+        search_equal(bt, 5, o, ps[5].iterations)
+        D_ok = is_perm(bt.read(5, "GB_TOUR"), 10000)
+        assert D_ok
+    finally:
+        bt.close()
