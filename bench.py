@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 HeatACO decoder (one JSON line on stdout).
+
+A step is one pass of the whole hot path over one batch: preparation
+(candidate lists, evidence, kappa, weights, T_NN, bounds) and every MMAS
+iteration (construction, iteration best, bounds, pheromone update + choice)
+of every instance.  Default workload: 128 symmetric instances, n ~ U{500..2000},
+50-NN synthetic heatmaps, m=64, k=20, 200 iterations.
+
+  value     ant-steps/s (sum of m*n*iterations / device time), inputs resident
+            in HBM, CUDA events on the decode stream, L2 flushed between steps
+  e2e       the same metric through hac_solve_batch with pinned host inputs:
+            H2D of the inputs and D2H of the best tours/lengths inside the
+            timed wall-clock region
+  roofline  construction kernel: algorithmic bytes (8*k_pad + 4 per ant-step)
+            over its CUDA-event time, against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+
+--impl reference times the CPU oracle (the only reference that exists for
+this method) on the same metric.  Under torchrun each rank decodes its own
+batch (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2601_19041_gb300 import synth  # noqa: E402
+
+WORKLOAD_TEXT = {
+    "batch128": "128 symmetric TSP instances, n~U{500..2000}, uniform points, 50-NN heatmap "
+                "w=exp(-d/dbar)*LogNormal(0,0.5) row-normalised, symmetrised in-library; "
+                "m=64 ants, k=20, alpha=1, beta=2, rho=0.2, 200 iterations, iteration-best deposit",
+    "tsp500": "1 symmetric TSP instance, n=500, 50-NN heatmap; m=50, k=20, rho=0.2, 100 iterations",
+    "atsp1000": "64 ATSP instances, n=1000, c_ij=||p_i-p_j||+U[0,0.5], directed 50-NN heatmap; "
+                "m=50, k=20, rho=0.2, d*=1, 200 iterations",
+    "tsp10k_2opt": "16 symmetric TSP instances, n=10000, 10-NN heatmap; m=64, k=10, rho=0.2, "
+                   "300 iterations, 2-opt on the iteration-best tour",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch128", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--apw", type=int, default=0, help="ants per warp (0 = library default)")
+    ap.add_argument("--wpb", type=int, default=0, help="construction warps per block")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="instances in the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=20, help="iterations in the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name, rank):
+    base = {"batch128": 1000, "atsp1000": 3000, "tsp10k_2opt": 2000, "tsp500": None}[name]
+    if name == "tsp500" or rank == 0:
+        return synth.workload(name)
+    return synth.workload(name, base_seed=base + 100000 * rank)
+
+
+def total_ant_steps(insts, ps, iters=None):
+    return int(sum(p.m * i.n * (p.iterations if iters is None else min(iters, p.iterations))
+                   for i, p in zip(insts, ps)))
+
+
+def algorithmic_construct_bytes(insts, ps):
+    """Bytes the construction must move per launch: per ant-step the candidate
+    row of choice_info and indices (8 B per padded slot) and the tour entry."""
+    return int(sum(p.m * i.n * (8 * (4 * ((p.k + 3) // 4)) + 4) for i, p in zip(insts, ps)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        busy = [x for x in sm if smax and x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(insts, ps, count, iters):
+    """Times the CPU oracle on the first `count` instances for `iters` iterations."""
+    import concurrent.futures as cf
+    from oracle import oracle as orc
+    orc.build()
+    import dataclasses
+    sub = [(insts[b], dataclasses.replace(ps[b], iterations=min(iters, ps[b].iterations)))
+           for b in range(min(count, len(insts)))]
+    cores = min(len(sub), os.cpu_count() or 1)
+
+    def one(ip):
+        o = orc.Oracle(ip[0], ip[1])
+        o.iterate(ip[1].iterations)
+        return o.scalars()["L_gb"]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:      # the C oracle releases the GIL
+        list(ex.map(one, sub))
+    dt = time.perf_counter() - t0
+    steps = total_ant_steps([s[0] for s in sub], [s[1] for s in sub])
+    return steps / dt, dt, cores, len(sub), steps
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    insts, ps = workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_sample(insts, ps, args.cpu_sample, 2)
+    vals, dts = [], []
+    for _ in range(args.steps):
+        v, dt, cores, cnt, steps = oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters)
+        vals.append(v)
+        dts.append(dt)
+    value = float(np.mean(vals))
+    sample = (f"first {cnt} instances of the workload, {args.cpu_iters} iterations each, "
+              f"preparation included, {steps} ant-steps per step")
+    print(json.dumps({
+        "impl": "reference", "metric": "ant-steps/s", "value": value, "unit": "ant-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * float(np.mean(dts)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOAD_TEXT[args.workload]},
+        "cpu_baseline": {"value": value, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "ant-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def device_instances(insts, torch):
+    out = []
+    for inst in insts:
+        d = synth.Instance(n=inst.n, kind=inst.kind,
+                           coords=None if inst.coords is None else torch.from_numpy(inst.coords).cuda(),
+                           cost=None if inst.cost is None else torch.from_numpy(inst.cost).cuda(),
+                           rowptr=torch.from_numpy(inst.rowptr).cuda(),
+                           col=torch.from_numpy(inst.col).cuda(),
+                           val=torch.from_numpy(inst.val).cuda(), symmetrize=inst.symmetrize)
+        out.append(d)
+    return out
+
+
+def input_bytes(insts):
+    tot = 0
+    for i in insts:
+        tot += (i.coords.nbytes if i.coords is not None else 0) + (i.cost.nbytes if i.cost is not None else 0)
+        tot += i.rowptr.nbytes + i.col.nbytes + i.val.nbytes
+    return int(tot)
+
+
+def run_ours(args):
+    import ctypes as C
+
+    import torch
+
+    from paper_2601_19041_gb300 import build, heataco
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    L = heataco._lib()
+    insts, ps = workload(args.workload, rank)
+    count = len(insts)
+    steps_per = total_ant_steps(insts, ps)
+    alg_bytes = algorithmic_construct_bytes(insts, ps)
+    stream = torch.cuda.Stream()
+    ex = heataco.make_exec(args.apw, args.wpb, use_graph=0, profile=1)
+
+    dins = device_instances(insts, torch)
+    m = heataco._Marshal(dins, ps, True)
+    ws_bytes = C.c_size_t(0)
+    heataco._check(L.hac_batch_workspace_size(m.ins, m.ps, count, 1, C.byref(ws_bytes)), "size")
+    ws = torch.empty(ws_bytes.value, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def one_step():
+        h = C.c_void_p()
+        heataco._check(L.hac_batch_create(m.ins, m.ps, count, 1, C.c_void_p(ws.data_ptr()), ws_bytes,
+                                          C.byref(ex), C.c_void_p(stream.cuda_stream), C.byref(h)), "create")
+        heataco._check(L.hac_batch_run(h), "run")
+        return h
+
+    def finish(h, stats):
+        heataco._check(L.hac_batch_sync(h), "sync")
+        ms0, k0 = C.c_double(), C.c_int64()
+        heataco._check(L.hac_batch_kernel_time(h, 0, C.byref(ms0), C.byref(k0)), "ktime")
+        nl = C.c_int64()
+        L.hac_batch_launches(h, C.byref(nl))
+        stats["construct_ms"] += ms0.value
+        stats["construct_launches"] += k0.value
+        stats["launches"] += nl.value
+        L.hac_batch_destroy(h)
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        finish(one_step(), {"construct_ms": 0.0, "construct_launches": 0, "launches": 0})
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    stats = {"construct_ms": 0.0, "construct_launches": 0, "launches": 0}
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        h = one_step()
+        e1.record(stream)
+        finish(h, stats)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_max = dev_ms
+    total_steps = steps_per * args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        s = torch.tensor([total_steps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        total_steps = float(s.item())
+        dist.barrier()
+    value = total_steps / (t_max / 1000.0)
+    inst_per_s = count * world * args.steps / (t_max / 1000.0)
+
+    # roofline of the construction kernel, from the live events of the timed steps
+    hbm_peak, peak_kind = load_peaks()
+    avg_ms = stats["construct_ms"] / max(stats["construct_launches"], 1)
+    per_launch_bytes = alg_bytes
+    achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
+    construct_share = stats["construct_ms"] / dev_ms if dev_ms else None
+
+    # end to end through hac_solve_batch with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        mh = heataco._Marshal(insts, ps, False, pin=True)
+        ws2 = C.c_size_t(0)
+        heataco._check(L.hac_batch_workspace_size(mh.ins, mh.ps, count, 0, C.byref(ws2)), "size")
+        if ws2.value > ws.numel():
+            ws = torch.empty(ws2.value, dtype=torch.uint8, device="cuda")
+        tours = [torch.empty(i.n, dtype=torch.int32, pin_memory=True) for i in insts]
+        tptr = (C.c_void_p * count)(*[t.data_ptr() for t in tours])
+        lens = torch.empty(count, dtype=torch.float64, pin_memory=True)
+        ex2 = heataco.make_exec(args.apw, args.wpb, use_graph=1)
+        stat = (C.c_int32 * count)()
+
+        def e2e_step():
+            heataco._check(L.hac_solve_batch(mh.ins, mh.ps, count, 0, C.c_void_p(ws.data_ptr()),
+                                             C.c_size_t(ws.numel()), C.byref(ex2), tptr,
+                                             C.c_void_p(lens.data_ptr()), stat,
+                                             C.c_void_p(stream.cuda_stream)), "solve_batch")
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        walls = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            walls.append(time.perf_counter() - t0)
+        w = sum(walls)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([w], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            w = float(t.item())
+        e2e = {"value": steps_per * world * args.steps / w, "unit": "ant-steps/s",
+               "h2d_bytes_per_step": input_bytes(insts),
+               "d2h_bytes_per_step": int(sum(4 * i.n for i in insts) + 8 * count),
+               "instances_per_s": count * world * args.steps / w}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, cores, cnt, st = oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters)
+        cpu = {"value": v, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {cnt} instances of the workload, {args.cpu_iters} iterations each, "
+                         f"preparation included ({st} ant-steps, {dt:.1f} s wall)"}
+
+    if rank == 0:
+        line = {
+            "metric": "ant-steps/s", "value": value, "unit": "ant-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOAD_TEXT[args.workload],
+                       "instances_per_gpu": count, "ant_steps_per_step_per_gpu": steps_per,
+                       "parallelism": f"instance batches, one per GPU ({world})",
+                       "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
+                       "inputs": "resident in HBM before the timed region",
+                       "ants_per_warp": ex.ants_per_warp or 4, "kernel_timing": "CUDA events per launch"},
+            "instances_per_s": inst_per_s,
+            "e2e": e2e,
+            "roofline": {"bound": "hbm", "kernel": "k_construct", "achieved": achieved,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                         "traffic": None,
+                         "algorithmic_bytes_per_launch": per_launch_bytes,
+                         "avg_launch_ms": avg_ms, "share_of_step": construct_share},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": stats["launches"],
+            "wall_s": wall,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

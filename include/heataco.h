@@ -57,9 +57,11 @@ enum hac_status {
  *           of the FP32 coordinates `coords` (n*2, x0 y0 x1 y1 ...).
  *   kind 1: explicit costs `cost` (n*n FP32 row-major, c_ij = cost[i*n+j]);
  *           directed (ATSP): the pheromone deposit is one-directional.
- * The heatmap H (eq. heatmap_def) is CSR: h_rowptr (n+1 int32, h_rowptr[0]=0),
- * h_col (nnz int32, strictly increasing within a row, no i==j), h_val (nnz
- * values in [0,1], FP32 when h_dtype==0, IEEE binary16 when h_dtype==1).
+ * The heatmap H (eq. heatmap_def) is CSR: h_rowptr (n+1 int32, h_rowptr[0]=0,
+ * h_rowptr[n]=h_nnz), h_col (h_nnz int32, strictly increasing within a row, no
+ * i==j), h_val (h_nnz values in [0,1], FP32 when h_dtype==0, IEEE binary16
+ * when h_dtype==1).  h_nnz is passed explicitly so that sizing never has to
+ * read device memory; a mismatch with h_rowptr[n] is HAC_EINVAL.
  * symmetrize=1 makes the decoder use (H + H^T)/2 (Sec. II-B). */
 typedef struct {
     int32_t n;
@@ -69,6 +71,7 @@ typedef struct {
     const int32_t *h_rowptr;
     const int32_t *h_col;
     const void *h_val;
+    int64_t h_nnz;
     int32_t h_dtype;
     int32_t symmetrize;
 } hac_instance;
@@ -103,6 +106,7 @@ typedef struct {
     int32_t use_graph;        /* 1: capture the iteration loop in a CUDA graph */
     int32_t fused;            /* 1: persistent fused construct+update kernel; 0: per-step launches */
     int32_t fallback_list;    /* nearest-unvisited lookup list length (0, 8, 16, 32); 0 = scan only */
+    int32_t profile;          /* 1: bracket every kernel group with CUDA events (no graphs) */
 } hac_exec;
 
 int hac_params_default(hac_params *p, int32_t kind);
@@ -124,9 +128,7 @@ int hac_version(void);
 typedef struct hac_batch hac_batch;
 
 /* Bytes of device workspace needed by hac_batch_create for these instances.
- * Validates sizes and parameters (not the heatmap contents).  Host-only,
- * except that with inputs_on_device==1 it reads h_rowptr[n] of each instance
- * from the device (a synchronous 4-byte copy). */
+ * Host-only; validates sizes and parameters (not the heatmap contents). */
 int hac_batch_workspace_size(const hac_instance *ins, const hac_params *ps, int32_t count,
                              int32_t inputs_on_device, size_t *bytes);
 
@@ -183,6 +185,16 @@ int hac_batch_results(hac_batch *bt, int32_t *const *best_tours, double *best_le
 
 /* Total ant-steps (sum of m*n*iterations done) and fallback steps so far. */
 int hac_batch_counters(hac_batch *bt, int64_t *ant_steps, int64_t *fallback_steps);
+
+/* Kernel launches this handle has issued (graph replays count the kernels
+ * they contain).  Host-side count; does not synchronise. */
+int hac_batch_launches(hac_batch *bt, int64_t *launches);
+
+/* With exec->profile==1: device time (ms, CUDA events on the handle's stream)
+ * and launch count of one kernel group since creation:
+ *   0 construction (Algorithm 2), 1 iteration tail (iteration best, 2-opt,
+ *   global best, pheromone update), 2 preparation.  Synchronises. */
+int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *launches);
 
 /* Releases the host handle; the workspace can be reused afterwards.  Does not
  * synchronise: the caller must not reuse the workspace before the stream has

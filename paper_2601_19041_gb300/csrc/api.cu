@@ -116,14 +116,9 @@ int instance_sizes(const hac_instance &in, const hac_params &p, int on_dev, Size
     z.ls_k = p.local_search ? p.ls_k : 0;
     z.sym = in.symmetrize;
     z.half = in.h_dtype;
-    int last = 0;
-    if (on_dev) {
-        cudaError_t e = cudaMemcpy(&last, in.h_rowptr + in.n, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) { g_last_cuda = (int)e; return HAC_ECUDA; }
-    } else {
-        last = in.h_rowptr[in.n];
-    }
-    if (last < 0) return HAC_EINVAL;
+    const long long last = in.h_nnz;
+    if (last < 0 || last > (1LL << 31) - 1) return HAC_EINVAL;
+    if (!on_dev && in.h_rowptr[in.n] != last) return HAC_EINVAL;
     if (last > 0 && (!in.h_col || !in.h_val)) return HAC_EINVAL;
     z.nnz = last;
     return HAC_OK;
@@ -244,7 +239,53 @@ struct hac_batch {
     bool any_ls = false;
     std::vector<int> t_host;
     cudaGraphExec_t gexec = nullptr;
+    int graph_kernels = 0;          // kernels inside one graph replay
+    long long launches = 0;         // kernels issued so far
+    // profiling: event pairs per kernel group, folded into totals on read
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_group;      // group of each recorded pair
+    double group_ms[3] = {0, 0, 0};
+    long long group_launches[3] = {0, 0, 0};
 };
+
+namespace {
+
+// records an event pair around the kernels `body` launches (profile mode)
+template <typename Body>
+int timed(hac_batch *bt, int group, Body &&body)
+{
+    if (!bt->ex.profile) return body();
+    while (bt->ev_pool.size() < bt->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return body();
+        bt->ev_pool.push_back(e);
+    }
+    cudaEvent_t a = bt->ev_pool[bt->ev_used], b = bt->ev_pool[bt->ev_used + 1];
+    cudaEventRecord(a, bt->stream);
+    int k = body();
+    cudaEventRecord(b, bt->stream);
+    bt->ev_used += 2;
+    bt->ev_group.push_back(group);
+    bt->group_launches[group] += k;
+    return k;
+}
+
+int fold_events(hac_batch *bt)
+{
+    if (!bt->ev_used) return HAC_OK;
+    CK(cudaStreamSynchronize(bt->stream));
+    for (size_t q = 0; q < bt->ev_group.size(); ++q) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, bt->ev_pool[2 * q], bt->ev_pool[2 * q + 1]));
+        bt->group_ms[bt->ev_group[q]] += ms;
+    }
+    bt->ev_used = 0;
+    bt->ev_group.clear();
+    return HAC_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -287,6 +328,7 @@ int hac_exec_default(hac_exec *e)
     e->use_graph = 1;
     e->fused = 0;
     e->fallback_list = 0;
+    e->profile = 0;
     return HAC_OK;
 }
 
@@ -366,6 +408,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
         D.degree_target = p.degree_target; D.local_search = p.local_search;
         D.baseline_scope = p.baseline_scope; D.symmetrize = in.symmetrize; D.h_half = in.h_dtype;
         D.seed = p.seed;
+        D.nnz = (int32_t)z.nnz;
         D.alpha = p.alpha; D.beta = p.beta; D.rho = p.rho; D.theta_h = p.theta_h; D.eps = p.eps;
         D.c_cap = p.c_cap; D.q_level = p.q_level; D.p_best = p.p_best; D.logw_clip = p.logw_clip;
         if (inputs_on_device) {
@@ -422,8 +465,10 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     CK(cudaMemcpyAsync(bt->d_warpmap, warpmap.data(), warpmap.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(bt->d_inst, bt->hi.data(), (size_t)count * sizeof(DevInst), cudaMemcpyHostToDevice, s));
 
-    launch_prep(bt->d_inst, bt->hi.data(), count, bt->d_rowmap, bt->rowmap_len, bt->d_slotmap,
-                bt->slotmap_len, bt->d_err, s);
+    bt->launches += timed(bt, 2, [&] {
+        return launch_prep(bt->d_inst, bt->hi.data(), count, bt->d_rowmap, bt->rowmap_len,
+                           bt->d_slotmap, bt->slotmap_len, bt->d_err, s);
+    });
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_last_cuda = (int)e;
@@ -441,11 +486,17 @@ static int remaining(const hac_batch *bt)
     return rem;
 }
 
-static void enqueue_iteration(hac_batch *bt)
+static int enqueue_iteration(hac_batch *bt)
 {
-    launch_iteration(bt->d_inst, bt->hi.data(), bt->count, bt->d_warpmap, bt->warpmap_len,
-                     bt->ex.ants_per_warp, bt->ex.warps_per_block, bt->max_n, bt->d_slotmap,
-                     bt->slotmap_len, bt->any_ls, bt->stream);
+    int k = timed(bt, 0, [&] {
+        return launch_construct(bt->d_inst, bt->d_warpmap, bt->warpmap_len, bt->ex.ants_per_warp,
+                                bt->ex.warps_per_block, bt->max_n, bt->stream);
+    });
+    k += timed(bt, 1, [&] {
+        return launch_iteration_tail(bt->d_inst, bt->count, bt->d_slotmap, bt->slotmap_len,
+                                     bt->any_ls, bt->stream);
+    });
+    return k;
 }
 
 int hac_batch_iterate(hac_batch *bt, int32_t iters)
@@ -454,11 +505,12 @@ int hac_batch_iterate(hac_batch *bt, int32_t iters)
     int todo = std::min(iters, remaining(bt));
     const int done = todo;
     cudaStream_t s = bt->stream;
-    if (bt->ex.use_graph && s != nullptr && todo >= GRAPH_CHUNK) {
+    if (bt->ex.use_graph && !bt->ex.profile && s != nullptr && todo >= GRAPH_CHUNK) {
         if (!bt->gexec) {
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            for (int q = 0; q < GRAPH_CHUNK; ++q) enqueue_iteration(bt);
+            bt->graph_kernels = 0;
+            for (int q = 0; q < GRAPH_CHUNK; ++q) bt->graph_kernels += enqueue_iteration(bt);
             cudaError_t e1 = cudaGetLastError();
             cudaError_t e2 = cudaStreamEndCapture(s, &g);
             if (e1 != cudaSuccess) { g_last_cuda = (int)e1; return HAC_ECUDA; }
@@ -469,10 +521,11 @@ int hac_batch_iterate(hac_batch *bt, int32_t iters)
         }
         while (todo >= GRAPH_CHUNK) {
             CK(cudaGraphLaunch(bt->gexec, s));
+            bt->launches += bt->graph_kernels;
             todo -= GRAPH_CHUNK;
         }
     }
-    for (; todo > 0; --todo) enqueue_iteration(bt);
+    for (; todo > 0; --todo) bt->launches += enqueue_iteration(bt);
     CK(cudaGetLastError());
     for (int b = 0; b < bt->count; ++b) bt->t_host[b] = std::min(bt->zs[b].iters, bt->t_host[b] + done);
     return HAC_OK;
@@ -578,10 +631,29 @@ int hac_batch_counters(hac_batch *bt, int64_t *ant_steps, int64_t *fallback_step
     return HAC_OK;
 }
 
+int hac_batch_launches(hac_batch *bt, int64_t *launches)
+{
+    if (!bt || !launches) return HAC_EINVAL;
+    *launches = bt->launches;
+    return HAC_OK;
+}
+
+int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *launches)
+{
+    if (!bt || group < 0 || group > 2) return HAC_EINVAL;
+    if (!bt->ex.profile) return HAC_EINVAL;
+    int st = fold_events(bt);
+    if (st) return st;
+    if (ms) *ms = bt->group_ms[group];
+    if (launches) *launches = bt->group_launches[group];
+    return HAC_OK;
+}
+
 int hac_batch_destroy(hac_batch *bt)
 {
     if (!bt) return HAC_EINVAL;
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    for (cudaEvent_t e : bt->ev_pool) cudaEventDestroy(e);
     delete bt;
     return HAC_OK;
 }

@@ -205,12 +205,13 @@ static void launch_construct_apw(const DevInst *d_inst, const int4 *d_warpmap, i
                                                                  nwords);
 }
 
-void launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
-                      int warps_per_block, int max_n, cudaStream_t s)
+int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
+                     int warps_per_block, int max_n, cudaStream_t s)
 {
     if (apw == 4) launch_construct_apw<4>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
     else if (apw == 2) launch_construct_apw<2>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
     else launch_construct_apw<1>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
+    return 1;
 }
 
 }  // namespace hac

@@ -42,6 +42,7 @@ struct DevInst {
     const int32_t *rowptr;    // n+1
     const int32_t *col;       // nnz
     const void *val;          // nnz (f32 or f16)
+    int32_t nnz;
     // transposed heatmap (symmetrize only): column i of H as a sorted row
     int32_t *trowptr, *tcol, *tfill;
     double *tval;
@@ -225,15 +226,13 @@ struct Launch {
 };
 
 // kernels (defined in the .cu files), launched by the host orchestration
-void launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const int2 *d_rowmap,
-                 int rowmap_len, const int2 *d_slotmap, int slotmap_len, int *d_err,
-                 cudaStream_t s);
-void launch_iteration(const DevInst *d_inst, const DevInst *h_inst, int count,
-                      const int4 *d_warpmap, int warpmap_len, int apw, int warps_per_block,
-                      int max_n, const int2 *d_slotmap, int slotmap_len, bool any_ls,
-                      cudaStream_t s);
-void launch_fused(const DevInst *d_inst, const DevInst *h_inst, int count, int iters,
-                  int apw, int max_n, int max_slots_per_inst, int *d_err, cudaStream_t s);
-bool fused_supported(const DevInst *h_inst, int count, int apw);
+// Each launcher returns the number of kernels it launched.
+int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const int2 *d_rowmap,
+                int rowmap_len, const int2 *d_slotmap, int slotmap_len, int *d_err,
+                cudaStream_t s);
+int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
+                     int warps_per_block, int max_n, cudaStream_t s);
+int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
+                          int slotmap_len, bool any_ls, cudaStream_t s);
 
 }  // namespace hac

@@ -36,8 +36,9 @@ __global__ void k_validate(const DevInst *insts, const int2 *rowmap, int *err)
     int lane = threadIdx.x & 31;
     if (i >= I.n) return;
     int b = I.rowptr[i], e = I.rowptr[i + 1];
-    if (lane == 0 && (b < 0 || e < b)) set_err(err, HAC_EINVAL);
-    if (b < 0 || e < b) return;
+    if (lane == 0 && (b < 0 || e < b || e > I.nnz || (i == 0 && b != 0) || (i == I.n - 1 && e != I.nnz)))
+        set_err(err, HAC_EINVAL);
+    if (b < 0 || e < b || e > I.nnz) return;
     for (int p = b + lane; p < e; p += 32) {
         int j = I.col[p];
         if (j < 0 || j >= I.n || j == i) set_err(err, HAC_EINVAL);
@@ -745,9 +746,9 @@ __global__ void k_init_tau(const DevInst *insts, const int2 *slotmap)
 // defined in twoopt.cu
 void launch_two_opt_nn(const DevInst *d_inst, int count, cudaStream_t s);
 
-void launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const int2 *d_rowmap,
-                 int rowmap_len, const int2 *d_slotmap, int slotmap_len, int *d_err,
-                 cudaStream_t s)
+int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const int2 *d_rowmap,
+                int rowmap_len, const int2 *d_slotmap, int slotmap_len, int *d_err,
+                cudaStream_t s)
 {
     int threads = ROW_WARPS * 32;
     bool any_sym = false, any_ls = false;
@@ -757,24 +758,29 @@ void launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const 
         any_ls |= h_inst[b].local_search != 0;
         max_n = h_inst[b].n > max_n ? h_inst[b].n : max_n;
     }
+    int launched = 0;
     k_validate<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap, d_err);
+    ++launched;
     if (any_sym) {
         k_tcount<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
         k_tscan<<<count, 1024, 0, s>>>(d_inst);
         k_tfill<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
         k_tsort<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
+        launched += 4;
     }
     k_members<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
     k_candidates<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
     k_evidence<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
     k_kappa<<<count, 1024, 0, s>>>(d_inst);
     k_weights<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
-    if (any_ls) k_nbr<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
+    launched += 5;
+    if (any_ls) { k_nbr<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap); ++launched; }
     size_t vis_bytes = (size_t)((max_n + 31) / 32) * 4;
     k_nn_tour<<<count, 1024, vis_bytes, s>>>(d_inst);
-    if (any_ls) launch_two_opt_nn(d_inst, count, s);
+    if (any_ls) { launch_two_opt_nn(d_inst, count, s); ++launched; }
     k_init_bounds<<<count, 256, 0, s>>>(d_inst);
     k_init_tau<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
+    return launched + 3;
 }
 
 }  // namespace hac

@@ -129,20 +129,16 @@ __global__ void k_update(const DevInst *insts, const int2 *slotmap)
     I.choice[s] = choice_value(I, tau, I.W[s]);
 }
 
-void launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
-                      int warps_per_block, int max_n, cudaStream_t s);
 void launch_two_opt_ib(const DevInst *d_inst, int count, cudaStream_t s);
 
-void launch_iteration(const DevInst *d_inst, const DevInst *h_inst, int count,
-                      const int4 *d_warpmap, int warpmap_len, int apw, int warps_per_block,
-                      int max_n, const int2 *d_slotmap, int slotmap_len, bool any_ls,
-                      cudaStream_t s)
+int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
+                          int slotmap_len, bool any_ls, cudaStream_t s)
 {
-    launch_construct(d_inst, d_warpmap, warpmap_len, apw, warps_per_block, max_n, s);
     k_select<<<count, 256, 0, s>>>(d_inst);
     if (any_ls) launch_two_opt_ib(d_inst, count, s);
     k_gb<<<count, 256, 0, s>>>(d_inst);
     k_update<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
+    return any_ls ? 4 : 3;
 }
 
 }  // namespace hac

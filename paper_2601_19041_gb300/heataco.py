@@ -35,7 +35,8 @@ class HeatACOError(RuntimeError):
 class hac_instance(C.Structure):
     _fields_ = [("n", C.c_int32), ("kind", C.c_int32), ("coords", C.c_void_p),
                 ("cost", C.c_void_p), ("h_rowptr", C.c_void_p), ("h_col", C.c_void_p),
-                ("h_val", C.c_void_p), ("h_dtype", C.c_int32), ("symmetrize", C.c_int32)]
+                ("h_val", C.c_void_p), ("h_nnz", C.c_int64), ("h_dtype", C.c_int32),
+                ("symmetrize", C.c_int32)]
 
 
 class hac_params(C.Structure):
@@ -49,7 +50,8 @@ class hac_params(C.Structure):
 
 class hac_exec(C.Structure):
     _fields_ = [("ants_per_warp", C.c_int32), ("warps_per_block", C.c_int32),
-                ("use_graph", C.c_int32), ("fused", C.c_int32), ("fallback_list", C.c_int32)]
+                ("use_graph", C.c_int32), ("fused", C.c_int32), ("fallback_list", C.c_int32),
+                ("profile", C.c_int32)]
 
 
 _LIB = None
@@ -73,6 +75,9 @@ SIGNATURES = {
     "hac_batch_results": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p]),
     "hac_batch_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "hac_batch_destroy": (C.c_int, [C.c_void_p]),
+    "hac_batch_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "hac_batch_kernel_time": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int64)]),
     "hac_solve": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_void_p,
                             C.c_size_t, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "hac_solve_batch": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_int32,
@@ -138,9 +143,10 @@ class _Marshal:
         return _np_ptr(arr)
 
     def _instance(self, inst, on_device, pin):
-        half = inst.val.dtype == np.float16
-        val = inst.val if len(inst.val) else np.zeros(1, inst.val.dtype)
-        col = inst.col if len(inst.col) else np.zeros(1, np.int32)
+        half = str(inst.val.dtype).endswith("float16")
+        nnz = int(len(inst.col))
+        val = inst.val if nnz else np.zeros(1, np.float16 if half else np.float32)
+        col = inst.col if nnz else np.zeros(1, np.int32)
         return hac_instance(
             inst.n, inst.kind,
             self._buf(inst.coords, np.float32, on_device, pin),
@@ -148,7 +154,7 @@ class _Marshal:
             self._buf(inst.rowptr, np.int32, on_device, pin),
             self._buf(col, np.int32, on_device, pin),
             self._buf(val, np.float16 if half else np.float32, on_device, pin),
-            1 if half else 0, int(inst.symmetrize))
+            nnz, 1 if half else 0, int(inst.symmetrize))
 
 
 def to_c_params(p) -> hac_params:
@@ -157,8 +163,8 @@ def to_c_params(p) -> hac_params:
                       p.baseline_scope, p.ls_k, p.seed)
 
 
-def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0):
-    return hac_exec(ants_per_warp, warps_per_block, use_graph, fused, fallback_list)
+def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0, profile=0):
+    return hac_exec(ants_per_warp, warps_per_block, use_graph, fused, fallback_list, profile)
 
 
 # ------------------------------------------------------------------ C-named calls
@@ -277,6 +283,17 @@ class Batch:
         a, f = C.c_int64(0), C.c_int64(0)
         _check(_lib().hac_batch_counters(self.h, C.byref(a), C.byref(f)), "hac_batch_counters")
         return a.value, f.value
+
+    def launches(self) -> int:
+        v = C.c_int64(0)
+        _check(_lib().hac_batch_launches(self.h, C.byref(v)), "hac_batch_launches")
+        return v.value
+
+    def kernel_time(self, group: int):
+        """(ms, launches) of kernel group 0 construction, 1 iteration tail, 2 preparation."""
+        ms, k = C.c_double(0), C.c_int64(0)
+        _check(_lib().hac_batch_kernel_time(self.h, group, C.byref(ms), C.byref(k)), "hac_batch_kernel_time")
+        return ms.value, k.value
 
 
 def solve_batch(instances, params, exec_=None, inputs_on_device=False):
