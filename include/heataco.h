@@ -213,6 +213,32 @@ int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count
                     const hac_exec *exec, int32_t *const *best_tours, double *best_lens,
                     int32_t *statuses, void *stream);
 
+/* ------------------------------------------------------------------ no allocation
+ * Decode one instance without any device allocation, for callers that cannot
+ * call cudaMalloc: a host application whose allocator or memory budget owns
+ * the free device memory, or a serving loop where an allocation could
+ * synchronise the device or fail under memory pressure.  (The paper has no
+ * counterpart; this is a property of the library, not of the method.)
+ *
+ * Same result as hac_solve on the same arguments.  The scratch is a fixed
+ * array of HAC_NOALLOC_MAX_BYTES compiled into the library: every GPU that
+ * loads the library holds it until the process exits.  An instance whose
+ * workspace (hac_batch_workspace_size) exceeds it is rejected with
+ * HAC_ENOMEM and nothing runs.  The call allocates no device memory (it uses
+ * no CUDA graph and no events); it uses a little host heap for its transient
+ * handle.  Inputs follow inputs_on_device as in hac_solve; best_tour (n
+ * int32) and best_len are host buffers.  The call synchronises `stream`.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.  All
+ * calls on a device share the one array and it keeps the previous call's
+ * contents; each call clears what must start at zero.  Calls that overlap on
+ * the GPU (other host threads, other streams) race on the array: serialise
+ * them. */
+#define HAC_NOALLOC_MAX_BYTES (16u << 20)
+int hac_solve_noalloc(const hac_instance *in, const hac_params *p, int32_t inputs_on_device,
+                      int32_t *best_tour, double *best_len, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,8 @@ SIGNATURES = {
     "hac_solve_batch": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_int32,
                                   C.c_void_p, C.c_size_t, C.POINTER(hac_exec), C.POINTER(C.c_void_p),
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "hac_solve_noalloc": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32,
+                                    C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
 }
 
 
