@@ -64,6 +64,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16, help="instances in the CPU sample")
     ap.add_argument("--cpu-iters", type=int, default=20, help="iterations in the CPU sample")
+    ap.add_argument("--count", type=int, default=0, help="use only the first COUNT instances (profiling)")
+    ap.add_argument("--fused", type=int, default=1, help="1: persistent fused cluster kernel")
+    ap.add_argument("--fbl", type=int, default=32, help="nearest-unvisited lookup list (0 or 32)")
+    ap.add_argument("--clog", type=int, default=0, help="fused: at least 2^clog CTAs per instance")
+    ap.add_argument("--plain-sample", type=int, default=4,
+                    help="instances decoded one per launch sequence for the plain-GPU comparison (0: skip)")
+    ap.add_argument("--iters", type=int, default=0, help="override the iteration count (profiling)")
     return ap.parse_args()
 
 
@@ -240,11 +247,18 @@ def run_ours(args):
     build.build()
     L = heataco._lib()
     insts, ps = workload(args.workload, rank)
+    if args.count:
+        insts, ps = insts[:args.count], ps[:args.count]
+    if args.iters:
+        for p in ps:
+            p.iterations = args.iters
     count = len(insts)
     steps_per = total_ant_steps(insts, ps)
     alg_bytes = algorithmic_construct_bytes(insts, ps)
     stream = torch.cuda.Stream()
-    ex = heataco.make_exec(args.apw, args.wpb, use_graph=0, profile=1)
+    ex = heataco.make_exec(args.apw, args.wpb, use_graph=0, profile=1, fused=args.fused,
+                           fallback_list=args.fbl, cluster_log2=args.clog)
+    kgroup = 3 if args.fused else 0
 
     dins = device_instances(insts, torch)
     m = heataco._Marshal(dins, ps, True)
@@ -263,7 +277,7 @@ def run_ours(args):
     def finish(h, stats):
         heataco._check(L.hac_batch_sync(h), "sync")
         ms0, k0 = C.c_double(), C.c_int64()
-        heataco._check(L.hac_batch_kernel_time(h, 0, C.byref(ms0), C.byref(k0)), "ktime")
+        heataco._check(L.hac_batch_kernel_time(h, kgroup, C.byref(ms0), C.byref(k0)), "ktime")
         nl = C.c_int64()
         L.hac_batch_launches(h, C.byref(nl))
         stats["construct_ms"] += ms0.value
@@ -312,12 +326,44 @@ def run_ours(args):
     value = total_steps / (t_max / 1000.0)
     inst_per_s = count * world * args.steps / (t_max / 1000.0)
 
-    # roofline of the construction kernel, from the live events of the timed steps
+    # roofline of the dominant kernel, from the live events of the timed steps.
+    # Fused: one launch runs every iteration (construction + update) of a group;
+    # its algorithmic bytes are the construction bytes of all iterations.
     hbm_peak, peak_kind = load_peaks()
-    avg_ms = stats["construct_ms"] / max(stats["construct_launches"], 1)
-    per_launch_bytes = alg_bytes
+    if args.fused:   # one region per step: the concurrent group launches of all iterations
+        avg_ms = stats["construct_ms"] / args.steps
+        per_launch_bytes = alg_bytes * ps[0].iterations
+    else:            # one construction launch per iteration
+        avg_ms = stats["construct_ms"] / max(stats["construct_launches"], 1)
+        per_launch_bytes = alg_bytes
     achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
     construct_share = stats["construct_ms"] / dev_ms if dev_ms else None
+    kernel_name = "k_fused (construct + update, all iterations)" if args.fused else "k_construct"
+
+    # the comparator: plain GPU MMAS, one instance per launch sequence
+    # (per-iteration kernels, CUDA graphs), on a sample of the same instances
+    plain = None
+    if args.plain_sample and rank == 0:
+        sub = list(range(min(args.plain_sample, count)))
+        exp = heataco.make_exec(2, 8, use_graph=1, fused=0, fallback_list=0)
+        tot_steps, tot_s = 0, 0.0
+        for b in sub:
+            mb = heataco._Marshal([dins[b]], [ps[b]], True)
+            wsb = C.c_size_t(0)
+            heataco._check(L.hac_batch_workspace_size(mb.ins, mb.ps, 1, 1, C.byref(wsb)), "size")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = C.c_void_p()
+            heataco._check(L.hac_batch_create(mb.ins, mb.ps, 1, 1, C.c_void_p(ws.data_ptr()), wsb,
+                                              C.byref(exp), C.c_void_p(stream.cuda_stream), C.byref(h)), "create")
+            heataco._check(L.hac_batch_run(h), "run")
+            heataco._check(L.hac_batch_sync(h), "sync")
+            tot_s += time.perf_counter() - t0
+            L.hac_batch_destroy(h)
+            tot_steps += total_ant_steps([insts[b]], [ps[b]])
+        plain = {"value": tot_steps / tot_s, "unit": "ant-steps/s",
+                 "sample": f"first {len(sub)} instances, each decoded alone (per-iteration kernels, CUDA graphs)",
+                 "speedup_of_batched": value / (tot_steps / tot_s)}
 
     # end to end through hac_solve_batch with pinned host buffers
     e2e = None
@@ -330,7 +376,8 @@ def run_ours(args):
         tours = [torch.empty(i.n, dtype=torch.int32, pin_memory=True) for i in insts]
         tptr = (C.c_void_p * count)(*[t.data_ptr() for t in tours])
         lens = torch.empty(count, dtype=torch.float64, pin_memory=True)
-        ex2 = heataco.make_exec(args.apw, args.wpb, use_graph=1)
+        ex2 = heataco.make_exec(args.apw, args.wpb, use_graph=1, fused=args.fused,
+                                fallback_list=args.fbl, cluster_log2=args.clog)
         stat = (C.c_int32 * count)()
 
         def e2e_step():
@@ -378,10 +425,12 @@ def run_ours(args):
                        "parallelism": f"instance batches, one per GPU ({world})",
                        "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
                        "inputs": "resident in HBM before the timed region",
-                       "ants_per_warp": ex.ants_per_warp or 4, "kernel_timing": "CUDA events per launch"},
+                       "ants_per_warp": ex.ants_per_warp or 4, "fused": args.fused,
+                       "fallback_list": args.fbl, "kernel_timing": "CUDA events per launch"},
             "instances_per_s": inst_per_s,
             "e2e": e2e,
-            "roofline": {"bound": "hbm", "kernel": "k_construct", "achieved": achieved,
+            "plain_gpu": plain,
+            "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "peak_kind": f"{peak_kind} HBM copy bandwidth",
                          "traffic": None,

@@ -105,8 +105,9 @@ typedef struct {
     int32_t warps_per_block;  /* construction block size in warps; 0 = auto */
     int32_t use_graph;        /* 1: capture the iteration loop in a CUDA graph */
     int32_t fused;            /* 1: persistent fused construct+update kernel; 0: per-step launches */
-    int32_t fallback_list;    /* nearest-unvisited lookup list length (0, 8, 16, 32); 0 = scan only */
+    int32_t fallback_list;    /* 32: look up the 32 nearest nodes (key order) before scanning; 0: scan only */
     int32_t profile;          /* 1: bracket every kernel group with CUDA events (no graphs) */
+    int32_t cluster_log2;     /* fused kernel: at least 2^cluster_log2 CTAs per instance (0 = fewest that fit) */
 } hac_exec;
 
 int hac_params_default(hac_params *p, int32_t kind);
@@ -193,7 +194,8 @@ int hac_batch_launches(hac_batch *bt, int64_t *launches);
 /* With exec->profile==1: device time (ms, CUDA events on the handle's stream)
  * and launch count of one kernel group since creation:
  *   0 construction (Algorithm 2), 1 iteration tail (iteration best, 2-opt,
- *   global best, pheromone update), 2 preparation.  Synchronises. */
+ *   global best, pheromone update), 2 preparation, 3 fused iterations
+ *   (construction and tail in the persistent cluster kernel).  Synchronises. */
 int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *launches);
 
 /* Releases the host handle; the workspace can be reused afterwards.  Does not

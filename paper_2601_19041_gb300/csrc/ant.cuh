@@ -1,0 +1,289 @@
+// One ant's tour (Algorithm 2), shared by the per-iteration kernel
+// (candidate rows in global memory) and the fused cluster kernel (rows in
+// shared / distributed shared memory).
+//
+// An ant is a segment of SEG = 32/APW lanes of a warp; all segments of a warp
+// advance in lockstep (same step s).  Per step, lanes g < k_pad/4 of a segment
+// hold candidate slots 4g..4g+3 (ids and choice values, one vector load each).
+//
+// Roulette (eq. transition): in-lane sequential partial sums, an inclusive
+// Hillis-Steele shuffle scan over the 8 lane totals (offsets 1, 2, 4), slot
+// prefix = exclusive lane prefix + in-lane partial sum; r = fl32(u * total)
+// selects the first live slot with r < prefix (ballot + ffs), or the last
+// live slot when rounding leaves none.
+//
+// Fallback (N_i empty): the nearest unvisited node by (FP32 key, index).  The
+// whole warp serves the segments that need it, one after the other: first the
+// node's 32-entry list of nearest nodes in key order (the first unvisited entry
+// of that list is the exact answer when there is one), else a scan of the
+// unvisited bits of the ant's mask.
+#pragma once
+
+#include "hac_internal.cuh"
+
+namespace hac {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int FBL = 32;   // fallback list length (nearest nodes in key order)
+
+__device__ __forceinline__ uint32_t word_of(const U4 &v, int w)
+{
+    return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ int int_of(const int4 &v, int w)
+{
+    return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
+}
+
+// candidate rows in global memory (int32 ids, FP32 choice)
+struct GlobalRows {
+    const int4 *cand4;
+    const float4 *ch4;
+    int G;
+    __device__ __forceinline__ void load(int cur, int g, int4 &id, float4 &ch) const
+    {
+        id = __ldg(cand4 + (size_t)cur * G + g);
+        ch = __ldg(ch4 + (size_t)cur * G + g);
+    }
+};
+
+// shared-memory loads by 32-bit shared-window address; for C > 1 the address
+// is first mapped to the owning CTA of the cluster (distributed shared memory)
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ uint2 ld_dsmem_u2(uint32_t a)
+{
+    uint2 v;
+    asm volatile("ld.shared::cluster.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ float4 ld_dsmem_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_smem_u2(uint32_t a)
+{
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ float4 ld_smem_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+// candidate rows in the shared memory of the CTAs of a cluster, interleaved by
+// row (row i lives in CTA i & (C-1) at local row i >> CLOG); uint16 ids with
+// 0xffff for padding.  Same layout (and offsets) in every CTA.
+template <int CLOG>
+struct ClusterRows {
+    uint32_t idx_base, ch_base;   // shared-window addresses in the calling CTA
+    int kp;
+    __device__ __forceinline__ void load(int cur, int g, int4 &id, float4 &chv) const
+    {
+        const uint32_t loc = (uint32_t)cur >> CLOG;
+        const uint32_t off = loc * (uint32_t)kp + 4u * (uint32_t)g;
+        uint32_t ia = idx_base + 2u * off, ca = ch_base + 4u * off;
+        uint2 raw;
+        if (CLOG == 0) {
+            raw = ld_smem_u2(ia);
+            chv = ld_smem_f4(ca);
+        } else {
+            const uint32_t owner = (uint32_t)cur & ((1u << CLOG) - 1u);
+            raw = ld_dsmem_u2(map_to_rank(ia, owner));
+            chv = ld_dsmem_f4(map_to_rank(ca, owner));
+        }
+        const int a0 = raw.x & 0xffff, a1 = raw.x >> 16, a2 = raw.y & 0xffff, a3 = raw.y >> 16;
+        id.x = a0 == 0xffff ? -1 : a0;
+        id.y = a1 == 0xffff ? -1 : a1;
+        id.z = a2 == 0xffff ? -1 : a2;
+        id.w = a3 == 0xffff ? -1 : a3;
+    }
+};
+
+// Builds the tours of the warp's APW ants (ants a = a_first + seg, real when
+// a < a_end) in iteration t.  vis_warp: APW bitmasks of `stride` words.
+// Returns the number of fallback steps of the calling lane's ant (lane sl==0).
+template <int APW, typename Rows>
+__device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &rows, int t, int a_first,
+                                                int a_end, unsigned *vis_warp, int stride,
+                                                const float2 *xy_scan)
+{
+    constexpr int SEG = 32 / APW;
+    constexpr unsigned SEGMASK = SEG == 32 ? 0xffffffffu : ((1u << SEG) - 1u);
+    const int lane = threadIdx.x & 31;
+    const int seg = lane / SEG, sl = lane % SEG, segbase = seg * SEG;
+    const int a = a_first + seg;
+    const bool real = a < a_end;
+    // instance fields in registers for the whole tour
+    const int n = I.n, kp = I.k_pad, G = kp >> 2, kind = I.kind;
+    const uint64_t seed = I.seed;
+    const double *__restrict__ cdist = I.cdist;
+    const int32_t *__restrict__ fbl = I.fbl;
+    const float *__restrict__ cost = I.cost;
+    const float2 *__restrict__ xy = xy_scan;   // coordinates for the fallback scan
+    const int nwords = (n + 31) >> 5;
+    unsigned *vis = vis_warp + seg * stride;
+
+    for (int w = sl; w < nwords; w += SEG) vis[w] = 0u;
+    __syncwarp();
+
+    uint32_t qbase = 0;
+    U4 rnd = draw_block(seed, (uint32_t)t, (uint32_t)(real ? a : 0), (uint32_t)sl);
+    const int start = (int)__umulhi(__shfl_sync(FULL_MASK, rnd.x, segbase), (uint32_t)n);
+    if (sl == 0 && real) vis[start >> 5] |= 1u << (start & 31);
+    __syncwarp();
+    int tb = sl == 0 ? start : 0;
+    int32_t *tour = I.tours + (size_t)(real ? a : 0) * n;
+    // L = ((d_1 + d_2) + ...) in step order; each d is added two steps after
+    // its load was issued, so the load latency never stalls the next step
+    double L = 0.0, dq1 = 0.0, dq2 = 0.0;
+    unsigned nfb = 0;
+    int cur = start;
+    // the row of the current node is loaded at the end of the previous step
+    int4 id = make_int4(-1, -1, -1, -1);
+    float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (real && sl < G) rows.load(cur, sl, id, ch);
+
+    for (int s = 1; s < n; ++s) {
+        auto unv = [&](int j) { return j >= 0 && !((vis[j >> 5] >> (j & 31)) & 1u); };
+        const float w0 = unv(id.x) ? ch.x : 0.0f;
+        const float w1 = unv(id.y) ? ch.y : 0.0f;
+        const float w2 = unv(id.z) ? ch.z : 0.0f;
+        const float w3 = unv(id.w) ? ch.w : 0.0f;
+        const float p0 = w0, p1 = __fadd_rn(p0, w1), p2 = __fadd_rn(p1, w2), p3 = __fadd_rn(p2, w3);
+        float inc = p3;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const float v = __shfl_up_sync(FULL_MASK, inc, o, 8);
+            if ((lane & 7) >= o) inc = __fadd_rn(inc, v);
+        }
+        const float ex = __shfl_up_sync(FULL_MASK, inc, 1, 8);
+        const bool g0 = (lane & 7) == 0;
+        const float S0 = g0 ? p0 : __fadd_rn(ex, p0);
+        const float S1 = g0 ? p1 : __fadd_rn(ex, p1);
+        const float S2 = g0 ? p2 : __fadd_rn(ex, p2);
+        const float S3 = g0 ? p3 : __fadd_rn(ex, p3);
+        const float total = __shfl_sync(FULL_MASK, inc, 7, SEG);
+
+        const bool anyw = (w0 > 0.0f) | (w1 > 0.0f) | (w2 > 0.0f) | (w3 > 0.0f);
+        const unsigned live_bits = (__ballot_sync(FULL_MASK, anyw) >> segbase) & SEGMASK;
+        const bool live = live_bits != 0u || !real;
+
+        const uint32_t q = (uint32_t)s >> 2;
+        if (q >= qbase + SEG) {
+            qbase += SEG;
+            rnd = draw_block(seed, (uint32_t)t, (uint32_t)(real ? a : 0), qbase + sl);
+        }
+        const uint32_t x = __shfl_sync(FULL_MASK, word_of(rnd, s & 3), (int)(q - qbase), SEG);
+        const float r = __fmul_rn(unif24(x), total);
+
+        int hq = -1;
+        if (w3 > 0.0f && r < S3) hq = 3;
+        if (w2 > 0.0f && r < S2) hq = 2;
+        if (w1 > 0.0f && r < S1) hq = 1;
+        if (w0 > 0.0f && r < S0) hq = 0;
+        const unsigned hit_bits = (__ballot_sync(FULL_MASK, hq >= 0) >> segbase) & SEGMASK;
+        const int lastq = w3 > 0.0f ? 3 : w2 > 0.0f ? 2 : w1 > 0.0f ? 1 : 0;
+        const int src = hit_bits ? __ffs(hit_bits) - 1 : 31 - __clz(live_bits | 1u);
+        const int myq = hit_bits ? (hq < 0 ? 0 : hq) : lastq;
+        // chosen node and slot in one shuffle: (node << 2) | slot-in-lane
+        const int packed = __shfl_sync(FULL_MASK, (int)(((unsigned)int_of(id, myq) << 2) | (unsigned)myq),
+                                       src, SEG);
+        int nxt = packed >> 2;
+        const int cq = packed & 3;
+
+        // ---- nearest unvisited node, one needing segment at a time, whole warp
+        unsigned need = __ballot_sync(FULL_MASK, sl == 0 && !live);
+        while (need) {
+            const int sb = __ffs(need) - 1;
+            need &= need - 1u;
+            const int scur = __shfl_sync(FULL_MASK, cur, sb);
+            const unsigned *sv = vis_warp + (sb / SEG) * stride;
+            int found = -1;
+            if (fbl) {
+                const int u = fbl[(size_t)scur * FBL + lane];
+                const bool ok = u >= 0 && !((sv[u >> 5] >> (u & 31)) & 1u);
+                const unsigned bm = __ballot_sync(FULL_MASK, ok);
+                if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
+            }
+            if (found < 0) {
+                float bk = __int_as_float(0x7f800000);
+                int bu = 0x7fffffff;
+                const float2 pc = kind == 0 ? xy[scur] : make_float2(0.f, 0.f);
+                const float *crow = kind == 1 ? cost + (size_t)scur * n : nullptr;
+                for (int w = lane; w < nwords; w += 32) {
+                    unsigned um = ~sv[w];
+                    if (w == nwords - 1 && (n & 31)) um &= (1u << (n & 31)) - 1u;
+                    while (um) {   // four unvisited nodes per round: independent loads
+                        int u4[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            u4[k] = um ? (w << 5) | (__ffs(um) - 1) : -1;
+                            um &= um - 1u;
+                        }
+                        float k4[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            k4[k] = u4[k] < 0 ? __int_as_float(0x7f800000)
+                                  : kind == 0 ? key32_xy(pc, xy[u4[k]]) : crow[u4[k]];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (u4[k] >= 0 && key_less(k4[k], u4[k], bk, bu)) { bk = k4[k]; bu = u4[k]; }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const float k2 = __shfl_xor_sync(FULL_MASK, bk, o);
+                    const int u2 = __shfl_xor_sync(FULL_MASK, bu, o);
+                    if (key_less(k2, u2, bk, bu)) { bk = k2; bu = u2; }
+                }
+                found = bu;
+            }
+            if (segbase == sb) nxt = found;
+        }
+        if ((unsigned)nxt >= (unsigned)n) nxt = 0;   // unreachable for finite keys; keeps indices in range
+
+        // next row first, so its latency overlaps the bookkeeping below
+        if (real && sl < G && s + 1 < n) rows.load(nxt, sl, id, ch);
+        if (sl == 0 && real) {
+            L = __dadd_rn(L, dq2);
+            dq2 = dq1;
+            if (!live) { dq1 = dist64(I, cur, nxt); ++nfb; }
+            else dq1 = cdist[(size_t)cur * kp + src * 4 + cq];
+            vis[nxt >> 5] |= 1u << (nxt & 31);
+        }
+        __syncwarp();
+        const int slot = s % SEG;
+        if (sl == slot) tb = nxt;
+        if (slot == SEG - 1 || s == n - 1) {
+            if (real && sl <= slot) tour[s - slot + sl] = tb;
+        }
+        cur = nxt;
+    }
+    if (sl == 0 && real) {
+        // the pipeline holds the last two edges (for n = 2 only one real edge)
+        L = __dadd_rn(L, dq2);
+        L = __dadd_rn(L, dq1);
+        L = __dadd_rn(L, dist64(I, cur, start));
+        I.lens[a] = L;
+    }
+    return nfb;
+}
+
+}  // namespace hac

@@ -28,6 +28,7 @@ thread_local int g_last_cuda = 0;
 constexpr int ROWS_PER_BLOCK = 8;      // matches the row kernels (8 warps, a row each)
 constexpr int SLOTS_PER_BLOCK = 1024;  // matches the slot kernels
 constexpr int GRAPH_CHUNK = 10;        // iterations per captured graph
+constexpr int FBL_LEN = 32;            // nearest-unvisited lookup list (ant.cuh FBL)
 
 struct Arena {
     size_t off = 0;
@@ -159,6 +160,7 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
         put("ls_pos", A.take(n * 4));
         put("ls_dlb", A.take(n));
     }
+    put("fbl", A.take(n * FBL_LEN * 4));
     put("nn_tour", A.take(n * 4));
     put("gb_tour", A.take(n * 4));
     put("ib_tour", A.take(n * 4));
@@ -211,6 +213,7 @@ int plan_batch(const hac_instance *ins, const hac_params *ps, int count, int on_
     A.take(rows * sizeof(int2));
     A.take(slots * sizeof(int2));
     A.take(warps * sizeof(int4));
+    A.take((size_t)count * sizeof(int32_t));   // fused-kernel cluster -> instance order
     size_t z0 = A.take(sizeof(int));       // error word starts the zero region
     for (const Sizes &z : P.zs) layout_zero(A, z, [](const char *, size_t) {});
     P.zero_bytes = A.off - z0;
@@ -220,6 +223,13 @@ int plan_batch(const hac_instance *ins, const hac_params *ps, int count, int on_
 }
 
 }  // namespace
+
+struct FusedGroup {
+    int clog = 0, count = 0, order_off = 0;
+    int rows_cap = 0, kp_cap = 0, stride = 0, warps = 0, xy_cap = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 
 struct hac_batch {
     int count = 0;
@@ -234,6 +244,8 @@ struct hac_batch {
     int slotmap_len = 0;
     int4 *d_warpmap = nullptr;
     int warpmap_len = 0;
+    int32_t *d_order = nullptr;
+    std::vector<FusedGroup> groups;   // non-empty when the fused kernel is used
     int *d_err = nullptr;
     int max_n = 0;
     bool any_ls = false;
@@ -245,8 +257,8 @@ struct hac_batch {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<int> ev_group;      // group of each recorded pair
-    double group_ms[3] = {0, 0, 0};
-    long long group_launches[3] = {0, 0, 0};
+    double group_ms[4] = {0, 0, 0, 0};
+    long long group_launches[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -286,6 +298,77 @@ int fold_events(hac_batch *bt)
 }
 
 }  // namespace
+
+// Groups the instances by cluster size (the fewest CTAs whose shared memory
+// holds the instance's share of the candidate table and visited masks, at
+// least 2^cluster_log2), each group ordered by decreasing work.
+static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
+{
+    const int apw = bt->ex.ants_per_warp == 2 ? 2 : 4;
+    bt->ex.ants_per_warp = apw;
+    const int count = bt->count;
+    std::vector<int> clog(count, -1);
+    auto fits = [&](int b, int cl, int &rows, int &warps) {
+        const Sizes &z = bt->zs[b];
+        const int C = 1 << cl;
+        rows = (z.n + C - 1) / C;
+        const int apc = (z.m + C - 1) / C;
+        warps = (apc + apw - 1) / apw;
+        if (warps > 16) return false;   // k_fused is compiled for at most 512 threads
+        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 31) / 32, 0) <= FUSED_SMEM_LIMIT;
+    };
+    for (int b = 0; b < count; ++b) {
+        if (bt->zs[b].n > 65534) return HAC_EUNSUPPORTED;
+        int rows, warps;
+        for (int cl = bt->ex.cluster_log2; cl <= 3; ++cl)
+            if (fits(b, cl, rows, warps)) { clog[b] = cl; break; }
+        if (clog[b] < 0) return HAC_EUNSUPPORTED;
+    }
+    for (;;) {   // group caps may exceed the limit when members differ: move a group up
+        bt->groups.clear();
+        bool again = false;
+        for (int cl = 0; cl <= 3 && !again; ++cl) {
+            FusedGroup G;
+            G.clog = cl;
+            for (int b = 0; b < count; ++b) {
+                if (clog[b] != cl) continue;
+                int rows, warps;
+                fits(b, cl, rows, warps);
+                G.count++;
+                G.rows_cap = std::max(G.rows_cap, rows);
+                G.kp_cap = std::max(G.kp_cap, bt->zs[b].kp);
+                G.stride = std::max(G.stride, (bt->zs[b].n + 31) / 32);
+                G.warps = std::max(G.warps, warps);
+            }
+            if (!G.count) continue;
+            const size_t base = fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, 0);
+            if (base > FUSED_SMEM_LIMIT) {
+                if (cl == 3) return HAC_EUNSUPPORTED;
+                for (int b = 0; b < count; ++b) if (clog[b] == cl) clog[b] = cl + 1;
+                again = true;
+                break;
+            }
+            // coordinates of the fallback scan in shared memory when they still fit
+            int nmax = 0;
+            for (int b = 0; b < count; ++b) if (clog[b] == cl) nmax = std::max(nmax, bt->zs[b].n);
+            if (base + (size_t)nmax * 8 <= FUSED_SMEM_LIMIT) G.xy_cap = nmax;
+            bt->groups.push_back(G);
+        }
+        if (!again) break;
+    }
+    order.clear();
+    for (FusedGroup &G : bt->groups) {
+        G.order_off = (int)order.size();
+        std::vector<int32_t> mem;
+        for (int b = 0; b < count; ++b) if (clog[b] == G.clog) mem.push_back(b);
+        std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) {
+            const Sizes &a = bt->zs[x], &c = bt->zs[y];
+            return (long long)a.m * a.n * a.iters > (long long)c.m * c.n * c.iters;
+        });
+        order.insert(order.end(), mem.begin(), mem.end());
+    }
+    return HAC_OK;
+}
 
 extern "C" {
 
@@ -329,6 +412,7 @@ int hac_exec_default(hac_exec *e)
     e->fused = 0;
     e->fallback_list = 0;
     e->profile = 0;
+    e->cluster_log2 = 0;
     return HAC_OK;
 }
 
@@ -363,6 +447,8 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     if (ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4) return HAC_EINVAL;
     if (ex.warps_per_block == 0) ex.warps_per_block = 4;
     if (ex.warps_per_block < 1 || ex.warps_per_block > 8) return HAC_EINVAL;
+    if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
+    if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
 
     hac_batch *bt = new (std::nothrow) hac_batch;
     if (!bt) return HAC_ENOMEM;
@@ -384,6 +470,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     bt->d_rowmap = (int2 *)(B + A.take(rows * sizeof(int2)));
     bt->d_slotmap = (int2 *)(B + A.take(slots * sizeof(int2)));
     bt->d_warpmap = (int4 *)(B + A.take(warps * sizeof(int4)));
+    bt->d_order = (int32_t *)(B + A.take((size_t)count * sizeof(int32_t)));
     size_t z0 = A.take(sizeof(int));
     bt->d_err = (int *)(B + z0);
     for (int b = 0; b < count; ++b) {
@@ -425,6 +512,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
             SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
             SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *)
             SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
+            SETP(fbl, int32_t *)
 #undef SETP
             if (!std::strcmp(name, "xy")) D.xy = (const float *)ptr;
             if (!std::strcmp(name, "cost")) D.cost = (const float *)ptr;
@@ -432,6 +520,8 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
             if (!std::strcmp(name, "col")) D.col = (const int32_t *)ptr;
             if (!std::strcmp(name, "val")) D.val = ptr;
         });
+        if (!ex.fallback_list) D.fbl = nullptr;
+        D.fbl_len = ex.fallback_list;
         if (!inputs_on_device) {
             const size_t n = z.n, nnz = (size_t)z.nnz;
             if (z.kind == 0) CK(cudaMemcpyAsync((void *)D.xy, in.coords, n * 8, cudaMemcpyHostToDevice, s));
@@ -464,6 +554,22 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     CK(cudaMemcpyAsync(bt->d_slotmap, slotmap.data(), slotmap.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(bt->d_warpmap, warpmap.data(), warpmap.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(bt->d_inst, bt->hi.data(), (size_t)count * sizeof(DevInst), cudaMemcpyHostToDevice, s));
+    if (bt->ex.fused) {
+        std::vector<int32_t> order;
+        if (plan_fused(bt, order) == HAC_OK) {
+            CK(cudaMemcpyAsync(bt->d_order, order.data(), order.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s));
+            for (size_t g = 1; g < bt->groups.size(); ++g) {
+                FusedGroup &G = bt->groups[g];
+                CK(cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming));
+            }
+        } else {
+            bt->ex.fused = 0;   // some instance does not fit the fused kernel: per-iteration path
+            bt->groups.clear();
+        }
+    }
 
     bt->launches += timed(bt, 2, [&] {
         return launch_prep(bt->d_inst, bt->hi.data(), count, bt->d_rowmap, bt->rowmap_len,
@@ -499,12 +605,50 @@ static int enqueue_iteration(hac_batch *bt)
     return k;
 }
 
+// the fused groups run concurrently: group 0 on the batch stream, the others on
+// side streams forked from and joined back into it
+static int enqueue_fused(hac_batch *bt, int iters)
+{
+    cudaError_t err = cudaSuccess;
+    const int k = timed(bt, 3, [&] {
+        cudaStream_t s = bt->stream;
+        for (size_t g = 1; g < bt->groups.size(); ++g) {
+            cudaEventRecord(bt->groups[g].fork, s);
+            cudaStreamWaitEvent(bt->groups[g].side, bt->groups[g].fork, 0);
+        }
+        for (size_t g = 0; g < bt->groups.size(); ++g) {
+            const FusedGroup &G = bt->groups[g];
+            cudaError_t e = launch_fused(bt->d_inst, bt->d_order + G.order_off, G.count, G.clog,
+                                         bt->ex.ants_per_warp, G.warps, G.rows_cap, G.kp_cap,
+                                         G.stride, G.xy_cap, iters, g ? G.side : s);
+            if (e != cudaSuccess && err == cudaSuccess) err = e;
+        }
+        for (size_t g = 1; g < bt->groups.size(); ++g) {
+            cudaEventRecord(bt->groups[g].join, bt->groups[g].side);
+            cudaStreamWaitEvent(s, bt->groups[g].join, 0);
+        }
+        return (int)bt->groups.size();
+    });
+    if (err != cudaSuccess) { g_last_cuda = (int)err; return HAC_ECUDA; }
+    bt->launches += k;
+    return HAC_OK;
+}
+
 int hac_batch_iterate(hac_batch *bt, int32_t iters)
 {
     if (!bt || iters < 0) return HAC_EINVAL;
     int todo = std::min(iters, remaining(bt));
     const int done = todo;
     cudaStream_t s = bt->stream;
+    if (bt->ex.fused && !bt->groups.empty()) {
+        if (todo > 0) {
+            int st = enqueue_fused(bt, todo);
+            if (st) return st;
+        }
+        CK(cudaGetLastError());
+        for (int b = 0; b < bt->count; ++b) bt->t_host[b] = std::min(bt->zs[b].iters, bt->t_host[b] + done);
+        return HAC_OK;
+    }
     if (bt->ex.use_graph && !bt->ex.profile && s != nullptr && todo >= GRAPH_CHUNK) {
         if (!bt->gexec) {
             cudaGraph_t g;
@@ -640,7 +784,7 @@ int hac_batch_launches(hac_batch *bt, int64_t *launches)
 
 int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *launches)
 {
-    if (!bt || group < 0 || group > 2) return HAC_EINVAL;
+    if (!bt || group < 0 || group > 3) return HAC_EINVAL;
     if (!bt->ex.profile) return HAC_EINVAL;
     int st = fold_events(bt);
     if (st) return st;
@@ -654,6 +798,11 @@ int hac_batch_destroy(hac_batch *bt)
     if (!bt) return HAC_EINVAL;
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
     for (cudaEvent_t e : bt->ev_pool) cudaEventDestroy(e);
+    for (FusedGroup &G : bt->groups) {
+        if (G.side) cudaStreamDestroy(G.side);
+        if (G.fork) cudaEventDestroy(G.fork);
+        if (G.join) cudaEventDestroy(G.join);
+    }
     delete bt;
     return HAC_OK;
 }

@@ -1,0 +1,189 @@
+// Persistent fused iteration kernel: one thread-block cluster per instance runs
+// whole MMAS iterations (Algorithm 1 lines 9-19) without leaving the GPU.
+//
+// Per instance the candidate table C_i (uint16 ids) and choice_info (FP32)
+// live in the shared memory of the cluster's C CTAs, interleaved by row (row
+// i in CTA i mod C).  Every construction step reads its row from local shared
+// memory or, through the cluster's distributed shared memory, from a
+// neighbouring SM, instead of from L2.  The ants are split over the CTAs, each
+// ant being a warp segment (ant.cuh).  Per iteration:
+//   construct (all CTAs) -> cluster barrier ->
+//   iteration best, optional 2-opt of T_ib, global best, bounds, succ/pred
+//   (CTA 0) -> cluster barrier ->
+//   bounded evaporation/deposit of every row, new choice_info written to
+//   shared memory (each CTA its own rows) -> cluster barrier.
+// Cluster barriers are hardware barriers (no spinning); all CTAs of a cluster
+// run the same number of iterations.  The arithmetic is exactly that of the
+// per-iteration kernels (ant.cuh, iter.cuh, twoopt.cuh).
+#include <cooperative_groups.h>
+
+#include "ant.cuh"
+#include "iter.cuh"
+#include "twoopt.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace hac {
+
+struct FusedArgs {
+    const DevInst *insts;
+    const int32_t *order;     // cluster -> instance
+    int iters_request;
+    int rows_cap;             // shared-memory rows per CTA (max over the group)
+    int kp_cap;               // max k_pad of the group
+    int stride;               // words per visited mask (max over the group)
+    int warps;                // warps per CTA
+    int apw;
+    int xy_cap;               // nodes whose coordinates fit in shared memory (0: read from global)
+};
+
+__host__ __device__ inline size_t fused_table_bytes(int rows_cap, int kp_cap)
+{
+    size_t ch = (size_t)rows_cap * kp_cap * 4;
+    size_t ix = ((size_t)rows_cap * kp_cap * 2 + 15) & ~(size_t)15;
+    return ch + ix;
+}
+
+template <int APW, int CLOG>
+__global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
+{
+    constexpr int C = 1 << CLOG;
+    constexpr int SEG = 32 / APW;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int cid = blockIdx.x >> CLOG;
+    const DevInst &I = A.insts[A.order[cid]];
+    InstState *st = I.st;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *sch = reinterpret_cast<float *>(smem);
+    uint16_t *sidx = reinterpret_cast<uint16_t *>(smem + (size_t)A.rows_cap * A.kp_cap * 4);
+    unsigned *svis = reinterpret_cast<unsigned *>(smem + fused_table_bytes(A.rows_cap, A.kp_cap));
+    float2 *sxy = reinterpret_cast<float2 *>(smem + fused_table_bytes(A.rows_cap, A.kp_cap) +
+                                             (size_t)A.warps * A.apw * A.stride * 4);
+
+    const int n = I.n, kp = I.k_pad, m = I.m;
+    const int R = (n + C - 1) >> CLOG;   // local rows: i = rank + C*l
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+
+    for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
+        const int l = e / kp, c = e - l * kp;
+        const int i = rank + (l << CLOG);
+        if (i < n) {
+            const int j = I.cand[(size_t)i * kp + c];
+            sidx[e] = j < 0 ? (uint16_t)0xffff : (uint16_t)j;
+            sch[e] = I.choice[(size_t)i * kp + c];
+        } else {
+            sidx[e] = 0xffff;
+            sch[e] = 0.0f;
+        }
+    }
+    const bool xy_shared = I.kind == 0 && I.n <= A.xy_cap;
+    if (xy_shared)
+        for (int e = threadIdx.x; e < n; e += blockDim.x) sxy[e] = reinterpret_cast<const float2 *>(I.xy)[e];
+    const float2 *xy_scan = xy_shared ? sxy : reinterpret_cast<const float2 *>(I.xy);
+    ClusterRows<CLOG> rows;
+    rows.idx_base = (uint32_t)__cvta_generic_to_shared(sidx);
+    rows.ch_base = (uint32_t)__cvta_generic_to_shared(sch);
+    rows.kp = kp;
+    const int t0 = st->t;
+    cl.sync();
+
+    const int t_end = min(I.iters, t0 + A.iters_request);
+    const int apc = (m + C - 1) >> CLOG;   // ants per CTA
+    const int a_lo = rank * apc, a_hi = min(m, a_lo + apc);
+    const float omega = __double2float_rn(__dsub_rn(1.0, I.rho));
+
+    for (int t = t0; t < t_end; ++t) {
+        const int a_first = a_lo + wib * APW;
+        if (a_first < a_hi) {
+            const unsigned nfb = build_tours<APW>(I, rows, t, a_first, a_hi,
+                                                  svis + (size_t)wib * APW * A.stride, A.stride, xy_scan);
+            if (lane % SEG == 0 && nfb) atomicAdd(&st->n_fallback, (unsigned long long)nfb);
+        }
+        __threadfence();
+        cl.sync();
+        if (rank == 0) {
+            block_iteration_best(I, st);
+            if (I.local_search) {
+                if (wib == 0) {
+                    warp_two_opt(I, I.ib_tour);
+                    const double L = warp_tour_length(I, I.ib_tour);
+                    if (lane == 0) st->L_ib = L;
+                }
+                __syncthreads();
+            }
+            block_global_best(I, st);
+            __threadfence();
+        }
+        cl.sync();
+        const float delta = __double2float_rn(__ddiv_rn(1.0, st->L_ib));
+        const float tmin = st->tau_min, tmax = st->tau_max;
+        for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
+            const int j = sidx[e];
+            if (j == 0xffff) continue;
+            const int l = e / kp, c = e - l * kp;
+            const int i = rank + (l << CLOG);
+            sch[e] = update_slot(I, (size_t)i * kp + c, i, j, omega, delta, tmin, tmax);
+        }
+        cl.sync();
+    }
+    for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
+        const int l = e / kp, c = e - l * kp;
+        const int i = rank + (l << CLOG);
+        if (i < n) I.choice[(size_t)i * kp + c] = sch[e];
+    }
+    cl.sync();
+}
+
+// ------------------------------------------------------------ host side
+
+template <int APW, int CLOG>
+static cudaError_t launch_fused_t(const FusedArgs &A, int clusters, int warps, size_t smem,
+                                  cudaStream_t s)
+{
+    auto kern = k_fused<APW, CLOG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters << CLOG), 1, 1);
+    cfg.blockDim = dim3((unsigned)(warps * 32), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1 << CLOG;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, A);
+}
+
+size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap)
+{
+    return fused_table_bytes(rows_cap, kp_cap) + (size_t)warps * apw * stride * 4 + (size_t)xy_cap * 8;
+}
+
+cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, int clusters, int clog,
+                         int apw, int warps, int rows_cap, int kp_cap, int stride, int xy_cap,
+                         int iters, cudaStream_t s)
+{
+    FusedArgs A{d_inst, d_order, iters, rows_cap, kp_cap, stride, warps, apw, xy_cap};
+    const size_t smem = fused_smem_bytes(rows_cap, kp_cap, warps, apw, stride, xy_cap);
+    if (apw == 2) {
+        switch (clog) {
+        case 0: return launch_fused_t<2, 0>(A, clusters, warps, smem, s);
+        case 1: return launch_fused_t<2, 1>(A, clusters, warps, smem, s);
+        case 2: return launch_fused_t<2, 2>(A, clusters, warps, smem, s);
+        default: return launch_fused_t<2, 3>(A, clusters, warps, smem, s);
+        }
+    }
+    switch (clog) {
+    case 0: return launch_fused_t<4, 0>(A, clusters, warps, smem, s);
+    case 1: return launch_fused_t<4, 1>(A, clusters, warps, smem, s);
+    case 2: return launch_fused_t<4, 2>(A, clusters, warps, smem, s);
+    default: return launch_fused_t<4, 3>(A, clusters, warps, smem, s);
+    }
+}
+
+}  // namespace hac

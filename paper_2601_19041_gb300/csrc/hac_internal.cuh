@@ -234,5 +234,11 @@ int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_l
                      int warps_per_block, int max_n, cudaStream_t s);
 int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
                           int slotmap_len, bool any_ls, cudaStream_t s);
+// fused cluster kernel (fused.cu): one cluster of 2^clog CTAs per instance
+size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap);
+cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, int clusters, int clog,
+                         int apw, int warps, int rows_cap, int kp_cap, int stride, int xy_cap,
+                         int iters, cudaStream_t s);
+constexpr size_t FUSED_SMEM_LIMIT = 220 * 1024;   // dynamic shared memory per CTA we allow
 
 }  // namespace hac

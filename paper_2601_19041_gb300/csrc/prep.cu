@@ -647,6 +647,39 @@ __global__ void k_nbr(const DevInst *insts, const int2 *rowmap)
     }
 }
 
+// ------------------------------------------------------------ nearest-unvisited lookup lists
+
+// For the fallback of Alg. 2: the 32 nodes u != i with the smallest
+// (FP32 key, u), ascending (-1 when n-1 < 32).  If one of them is unvisited,
+// the first unvisited one is the nearest unvisited node, exactly.
+__global__ void k_fbl(const DevInst *insts, const int2 *rowmap)
+{
+    int2 rm = rowmap[blockIdx.x];
+    const DevInst &I = insts[rm.x];
+    if (!I.fbl) return;
+    const int i = rm.y + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (i >= I.n) return;
+    const float2 *xy = reinterpret_cast<const float2 *>(I.xy);
+    const float2 pi = I.kind == 0 ? xy[i] : make_float2(0.f, 0.f);
+    const int K = I.n - 1 < 32 ? I.n - 1 : 32;
+    float pk = -1.0f;
+    int pu = -1, mine = -1;
+    for (int r = 0; r < K; ++r) {
+        float bk = __int_as_float(0x7f800000);
+        int bu = 0x7fffffff;
+        for (int u = lane; u < I.n; u += 32) {
+            if (u == i) continue;
+            const float kk = I.kind == 0 ? key32_xy(pi, xy[u]) : I.cost[(size_t)i * I.n + u];
+            if (key_less(pk, pu, kk, u) && key_less(kk, u, bk, bu)) { bk = kk; bu = u; }
+        }
+        warp_min_kj(bk, bu);
+        if (lane == r) mine = bu;
+        pk = bk;
+        pu = bu;
+    }
+    I.fbl[(size_t)i * 32 + lane] = lane < K ? mine : -1;
+}
+
 // ------------------------------------------------------------ T_NN
 
 // Nearest-neighbour tour from node 0 (one block per instance): each step takes
@@ -712,9 +745,11 @@ __device__ __forceinline__ void set_bounds(const DevInst &I, InstState *st, doub
     st->tau_min = __double2float_rn(tmin);
 }
 
+// fl32(tau^alpha * W); for alpha = 1 the exact FP64 product rounded once is the FP32 product
 __device__ __forceinline__ float choice_of(const DevInst &I, float tau, float W)
 {
-    double a = I.alpha == 1.0 ? (double)tau : det_exp(__dmul_rn(I.alpha, det_ln((double)tau)));
+    if (I.alpha == 1.0) return __fmul_rn(tau, W);
+    double a = det_exp(__dmul_rn(I.alpha, det_ln((double)tau)));
     return __double2float_rn(__dmul_rn(a, (double)W));
 }
 
@@ -773,7 +808,8 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
     k_evidence<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
     k_kappa<<<count, 1024, 0, s>>>(d_inst);
     k_weights<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
-    launched += 5;
+    k_fbl<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
+    launched += 6;
     if (any_ls) { k_nbr<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap); ++launched; }
     size_t vis_bytes = (size_t)((max_n + 31) / 32) * 4;
     k_nn_tour<<<count, 1024, vis_bytes, s>>>(d_inst);

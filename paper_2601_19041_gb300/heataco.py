@@ -51,7 +51,7 @@ class hac_params(C.Structure):
 class hac_exec(C.Structure):
     _fields_ = [("ants_per_warp", C.c_int32), ("warps_per_block", C.c_int32),
                 ("use_graph", C.c_int32), ("fused", C.c_int32), ("fallback_list", C.c_int32),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("cluster_log2", C.c_int32)]
 
 
 _LIB = None
@@ -165,8 +165,9 @@ def to_c_params(p) -> hac_params:
                       p.baseline_scope, p.ls_k, p.seed)
 
 
-def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0, profile=0):
-    return hac_exec(ants_per_warp, warps_per_block, use_graph, fused, fallback_list, profile)
+def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0, profile=0,
+              cluster_log2=0):
+    return hac_exec(ants_per_warp, warps_per_block, use_graph, fused, fallback_list, profile, cluster_log2)
 
 
 # ------------------------------------------------------------------ C-named calls
@@ -292,7 +293,8 @@ class Batch:
         return v.value
 
     def kernel_time(self, group: int):
-        """(ms, launches) of kernel group 0 construction, 1 iteration tail, 2 preparation."""
+        """(ms, launches) of kernel group 0 construction, 1 iteration tail, 2 preparation,
+        3 fused iterations."""
         ms, k = C.c_double(0), C.c_int64(0)
         _check(_lib().hac_batch_kernel_time(self.h, group, C.byref(ms), C.byref(k)), "hac_batch_kernel_time")
         return ms.value, k.value

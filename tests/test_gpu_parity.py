@@ -111,11 +111,33 @@ def test_case_parity(hac, orc, name):
     run_case(hac, orc, [inst], [p])
 
 
-@pytest.mark.parametrize("apw,wpb,graph", [(1, 4, 1), (2, 8, 0), (4, 2, 1), (4, 8, 0)])
-def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph):
+@pytest.mark.parametrize("apw,wpb,graph,fbl", [(1, 4, 1, 0), (2, 8, 0, 32), (4, 2, 1, 32), (4, 8, 0, 0)])
+def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph, fbl):
     inst = synth.euclid_instance(31, 410, K=50)
     p = params(m=21, k=20, iterations=23, rho=0.2, seed=3)
-    run_case(hac, orc, [inst], [p], exec_=hac.make_exec(apw, wpb, graph))
+    run_case(hac, orc, [inst], [p], exec_=hac.make_exec(apw, wpb, graph, fallback_list=fbl))
+
+
+FUSED = [dict(apw=2, clog=0, fbl=32), dict(apw=4, clog=1, fbl=0), dict(apw=4, clog=3, fbl=32),
+         dict(apw=2, clog=2, fbl=32)]
+
+
+@pytest.mark.parametrize("cfg", FUSED, ids=lambda c: f"apw{c['apw']}_C{1 << c['clog']}_fbl{c['fbl']}")
+@pytest.mark.parametrize("name", ["sym50nn_k20", "sym10nn_k10_ragged", "k32", "k7_pad", "n3",
+                                  "empty_heatmap", "atsp", "two_opt", "alpha_beta_powers"])
+def test_fused_kernel_parity(hac, orc, name, cfg):
+    inst, p = CASES[name]()
+    ex = hac.make_exec(cfg["apw"], 0, 1, fused=1, fallback_list=cfg["fbl"], cluster_log2=cfg["clog"])
+    run_case(hac, orc, [inst], [p], exec_=ex)
+
+
+def test_fused_mixed_batch_groups(hac, orc):
+    # different sizes land in different cluster-size groups that run concurrently
+    insts, ps = [], []
+    for b, (n, k, m) in enumerate([(90, 20, 9), (1900, 20, 40), (4000, 12, 20), (333, 10, 17), (12, 8, 5)]):
+        insts.append(synth.euclid_instance(70 + b, n, K=20))
+        ps.append(params(m=m, k=k, iterations=3 + b, rho=0.2, seed=170 + b))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(4, 0, 1, fused=1, fallback_list=32))
 
 
 def test_mixed_batch_parity(hac, orc):
@@ -156,6 +178,7 @@ def test_batch_membership_does_not_change_results(hac):
 def test_full_size_tsp500(hac, orc):
     insts, ps = synth.workload("tsp500")
     run_case(hac, orc, insts, ps)
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(**BENCH_EXEC))
 
 
 def _oracle_many(orc, insts, ps):
@@ -166,10 +189,13 @@ def _oracle_many(orc, insts, ps):
         return list(ex.map(one, range(len(insts))))
 
 
+BENCH_EXEC = dict(ants_per_warp=4, fused=1, fallback_list=32)   # what bench.py times by default
+
+
 @pytest.mark.parametrize("name,sample", [("batch128", (0, 37, 90, 127)), ("atsp1000", (0, 31, 63))])
 def test_full_size_workload_sampled(hac, orc, name, sample):
     insts, ps = synth.workload(name)
-    bt = hac.Batch(insts, ps)
+    bt = hac.Batch(insts, ps, hac.make_exec(**BENCH_EXEC))
     try:
         bt.run().sync()
         sub_i = [insts[b] for b in sample]
@@ -183,7 +209,7 @@ def test_full_size_workload_sampled(hac, orc, name, sample):
 
 def test_full_size_tsp10k_two_opt_sampled(hac, orc):
     insts, ps = synth.workload("tsp10k_2opt")
-    bt = hac.Batch(insts, ps)
+    bt = hac.Batch(insts, ps, hac.make_exec(**BENCH_EXEC))
     try:
         bt.run().sync()
         o = _oracle_many(orc, [insts[5]], [ps[5]])[0]
