@@ -531,13 +531,26 @@ int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour
 
 /* ------------------------------------------------------------ tour length */
 
-/* Eq. (tour_length), accumulated in FP64 in tour order, closing edge last. */
+/* Eq. (tour_length) in FP64.  Reading: the paper fixes no summation order.
+ * The n edges in visiting order (edge e joins tour[e] and tour[e+1], the
+ * closing edge last) are summed in consecutive blocks of 32; a block by the
+ * pairwise tree (adjacent pairs, then pairs of pair sums, five levels, with
+ * missing edges as +0), and the block sums are then added in order. */
 double orc_tour_length(const orc_instance *in, const int32_t *tour)
 {
     int n = in->n;
     double L = 0.0;
-    for (int s = 1; s < n; ++s) L = L + orc_dist(in, tour[s - 1], tour[s]);
-    return L + orc_dist(in, tour[n - 1], tour[0]);
+    for (int b = 0; b < n; b += 32) {
+        double v[32];
+        for (int q = 0; q < 32; ++q) {
+            int e = b + q;
+            v[q] = e < n ? orc_dist(in, tour[e], tour[(e + 1) % n]) : 0.0;
+        }
+        for (int w = 1; w < 32; w *= 2)
+            for (int q = 0; q < 32; q += 2 * w) v[q] = v[q] + v[q + w];
+        L = L + v[0];
+    }
+    return L;
 }
 
 /* ---------------------------------------------- nearest-neighbour tour T_NN */
@@ -643,7 +656,6 @@ static void construct(orc_state *S, int a, int32_t *T, double *Lout)
     int start = (int)(((uint64_t)x0 * (uint64_t)n) >> 32);   /* random start node */
     T[0] = start;
     S->visited[start] = 1;
-    double L = 0.0;
     float w[ORC_KMAX];
     for (int s = 1; s < n; ++s) {
         int i = T[s - 1];
@@ -654,22 +666,18 @@ static void construct(orc_state *S, int a, int32_t *T, double *Lout)
             if (w[c] > 0.0f) any = 1;
         }
         int j;
-        double d;
         if (any) {
             float u = unif24(orc_draw(S->p.seed, t, (uint32_t)a, (uint32_t)s));
             int c = orc_roulette(w, kp, u);
             j = S->cand[(int64_t)i * kp + c];
-            d = S->cdist[(int64_t)i * kp + c];
         } else {                                         /* nearest unvisited node */
             j = nearest_unvisited(in, S->visited, i);
-            d = orc_dist(in, i, j);
             S->n_fallback++;
         }
-        L = L + d;
         T[s] = j;
         S->visited[j] = 1;
     }
-    *Lout = L + orc_dist(in, T[n - 1], T[0]);
+    *Lout = orc_tour_length(in, T);
 }
 
 /* ------------------------------------------------- one iteration (Alg. 1) */

@@ -54,6 +54,22 @@ def tour_len(D, tour):
     return L + D[tour[-1], tour[0]]
 
 
+def blocked_pairwise_len(D, tour):
+    """The decoder's tour-length order, restated: edges in visiting order,
+    blocks of 32 summed as pairwise trees, block sums added in order."""
+    n = len(tour)
+    L = 0.0
+    for b in range(0, n, 32):
+        v = [float(D[tour[e], tour[(e + 1) % n]]) if e < n else 0.0 for e in range(b, b + 32)]
+        w = 1
+        while w < 32:
+            for q in range(0, 32, 2 * w):
+                v[q] = v[q] + v[q + w]
+            w *= 2
+        L = L + v[0]
+    return L
+
+
 def brute_force_opt(D):
     """Exact optimum by enumerating (n-1)!/2 cycles (node 0 fixed)."""
     n = D.shape[0]
