@@ -532,25 +532,19 @@ int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour
 /* ------------------------------------------------------------ tour length */
 
 /* Eq. (tour_length) in FP64.  Reading: the paper fixes no summation order.
- * The n edges in visiting order (edge e joins tour[e] and tour[e+1], the
- * closing edge last) are summed in consecutive blocks of 32; a block by the
- * pairwise tree (adjacent pairs, then pairs of pair sums, five levels, with
- * missing edges as +0), and the block sums are then added in order. */
+ * Edge e joins tour[e] and tour[e+1] (the closing edge is e = n-1).  Edge e
+ * goes to partial sum P[e mod 32]; each partial adds its edges in increasing
+ * e, starting from 0; the 32 partials are then combined by the pairwise tree
+ * (adjacent pairs, then pairs of pair sums, five levels). */
 double orc_tour_length(const orc_instance *in, const int32_t *tour)
 {
     int n = in->n;
-    double L = 0.0;
-    for (int b = 0; b < n; b += 32) {
-        double v[32];
-        for (int q = 0; q < 32; ++q) {
-            int e = b + q;
-            v[q] = e < n ? orc_dist(in, tour[e], tour[(e + 1) % n]) : 0.0;
-        }
-        for (int w = 1; w < 32; w *= 2)
-            for (int q = 0; q < 32; q += 2 * w) v[q] = v[q] + v[q + w];
-        L = L + v[0];
-    }
-    return L;
+    double P[32];
+    for (int q = 0; q < 32; ++q) P[q] = 0.0;
+    for (int e = 0; e < n; ++e) P[e % 32] = P[e % 32] + orc_dist(in, tour[e], tour[(e + 1) % n]);
+    for (int w = 1; w < 32; w *= 2)
+        for (int q = 0; q < 32; q += 2 * w) P[q] = P[q] + P[q + w];
+    return P[0];
 }
 
 /* ---------------------------------------------- nearest-neighbour tour T_NN */

@@ -54,20 +54,19 @@ def tour_len(D, tour):
     return L + D[tour[-1], tour[0]]
 
 
-def blocked_pairwise_len(D, tour):
-    """The decoder's tour-length order, restated: edges in visiting order,
-    blocks of 32 summed as pairwise trees, block sums added in order."""
+def strided_partials_len(D, tour):
+    """The decoder's tour-length order, restated: edge e into partial e mod 32
+    (sequential within a partial), then a pairwise tree over the 32 partials."""
     n = len(tour)
-    L = 0.0
-    for b in range(0, n, 32):
-        v = [float(D[tour[e], tour[(e + 1) % n]]) if e < n else 0.0 for e in range(b, b + 32)]
-        w = 1
-        while w < 32:
-            for q in range(0, 32, 2 * w):
-                v[q] = v[q] + v[q + w]
-            w *= 2
-        L = L + v[0]
-    return L
+    P = [0.0] * 32
+    for e in range(n):
+        P[e % 32] = P[e % 32] + float(D[tour[e], tour[(e + 1) % n]])
+    w = 1
+    while w < 32:
+        for q in range(0, 32, 2 * w):
+            P[q] = P[q] + P[q + w]
+        w *= 2
+    return P[0]
 
 
 def brute_force_opt(D):

@@ -9,7 +9,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
-from helpers import (blocked_pairwise_len, brute_force_opt, cycle_heat, dmat, euclid, is_perm, params,
+from helpers import (strided_partials_len, brute_force_opt, cycle_heat, dmat, euclid, is_perm, params,
                      tour_len)
 
 
@@ -144,7 +144,7 @@ def test_invariants_every_iteration(orc):
         for a in range(p.m):
             assert is_perm(tours[a], inst.n)
             assert lens[a] == pytest.approx(tour_len(D, tours[a]), rel=1e-14)
-            assert lens[a] == blocked_pairwise_len(D, tours[a])   # the stated order, bitwise
+            assert lens[a] == strided_partials_len(D, tours[a])   # the stated order, bitwise
         ib = int(np.argmin(lens))
         assert o.get("trace_ib")[t] == ib
         assert s["L_gb"] <= prev_gb and s["L_gb"] <= s0["L_nn"]
@@ -196,16 +196,16 @@ def test_atsp_deposits_one_orientation(orc):
 
 
 def test_tour_length_order_and_accuracy(orc):
-    """The blocked pairwise FP64 sum: exact on integer edge lengths, within the
-    pairwise error bound of the exact (rational) sum otherwise, and not the
-    sequential order."""
+    """The strided-partials FP64 sum: exact on integer edge lengths, within the
+    error bound of its order (n/32 sequential adds, then a 5-level tree) of the
+    exact (rational) sum otherwise."""
     from fractions import Fraction
     m = 8
     pts = np.array([(x, y) for y in range(m) for x in range(m)], np.float32)
     cyc = list(range(m * m))       # row-major snake is not a grid tour; any permutation works
     inst = euclid(pts)
     D = dmat(pts)
-    assert orc.tour_length(inst, cyc) == blocked_pairwise_len(D, cyc)
+    assert orc.tour_length(inst, cyc) == strided_partials_len(D, cyc)
     rng = np.random.default_rng(12)
     for n in (3, 31, 32, 33, 100, 1000):
         P = rng.random((n, 2)).astype(np.float32)
@@ -214,7 +214,7 @@ def test_tour_length_order_and_accuracy(orc):
         t = rng.permutation(n)
         L = orc.tour_length(inst, t)
         exact = sum(Fraction(D[t[e], t[(e + 1) % n]]) for e in range(n))
-        bound = (5 + n / 32 + 2) * 2.0 ** -53 * float(exact)
+        bound = (5 + math.ceil(n / 32) + 2) * 2.0 ** -53 * float(exact)
         assert abs(Fraction(L) - exact) <= Fraction(bound)
     # four unit edges: (1 + 1) + (1 + 1) = 4 exactly
     sq = euclid(np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32))
@@ -290,5 +290,5 @@ def test_local_search_run_keeps_invariants(orc):
     ib = o.get("ib_tour")
     assert is_perm(ib, inst.n)
     assert _two_opt_gain_left(D, ib, nbr) <= 1e-9
-    assert o.scalars()["L_ib"] == blocked_pairwise_len(D, ib)
+    assert o.scalars()["L_ib"] == strided_partials_len(D, ib)
     assert o.scalars()["L_gb"] <= s0["L_nn"]
