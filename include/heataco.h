@@ -51,6 +51,7 @@ enum hac_status {
 
 #define HAC_KMAX 32         /* candidate-list size limit (one 8-lane warp segment) */
 #define HAC_NMAX (1 << 20)  /* node-count limit of one instance */
+#define HAC_MMAX 1024       /* ants per instance */
 
 /* One decode problem (Sec. II-A, II-B).
  *   kind 0: symmetric Euclidean; d_ij = sqrt((x_j-x_i)^2 + (y_j-y_i)^2) in FP64

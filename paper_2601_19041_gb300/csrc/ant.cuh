@@ -19,7 +19,7 @@
 // unvisited bits of the ant's mask.
 #pragma once
 
-#include "hac_internal.cuh"
+#include "lengths.cuh"
 
 namespace hac {
 
@@ -116,13 +116,40 @@ struct ClusterRows {
     }
 };
 
+// nearest-unvisited lookup lists: global int32 (I.fbl) or the uint16 copy in
+// the cluster's shared memory (same row interleaving as the candidate table)
+struct GlobalList {
+    const int32_t *fbl;
+    __device__ __forceinline__ bool present() const { return fbl != nullptr; }
+    __device__ __forceinline__ int get(int node, int k) const { return fbl[(size_t)node * FBL + k]; }
+};
+
+template <int CLOG>
+struct ClusterList {
+    uint32_t base;   // shared-window address of this CTA's list rows (0: no list)
+    __device__ __forceinline__ bool present() const { return base != 0u; }
+    __device__ __forceinline__ int get(int node, int k) const
+    {
+        const uint32_t loc = (uint32_t)node >> CLOG;
+        uint32_t a = base + 2u * (loc * FBL + (uint32_t)k);
+        unsigned short v;
+        if (CLOG == 0) asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+        else {
+            a = map_to_rank(a, (uint32_t)node & ((1u << CLOG) - 1u));
+            asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(a));
+        }
+        return v == 0xffff ? -1 : (int)v;
+    }
+};
+
 // Builds the tours of the warp's APW ants (ants a = a_first + seg, real when
 // a < a_end) in iteration t.  vis_warp: APW bitmasks of `stride` words.
-// Returns the number of fallback steps of the calling lane's ant (lane sl==0).
-template <int APW, typename Rows>
-__device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &rows, int t, int a_first,
-                                                int a_end, unsigned *vis_warp, int stride,
-                                                const float2 *xy_scan)
+// Tours (and the chosen slot of every step, 0xff for a nearest-unvisited
+// step) are written ant-major; lengths are summed afterwards (lengths.cuh).
+template <int APW, typename Rows, typename List>
+__device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, const List &list, int t,
+                                            int a_first, int a_end, unsigned *vis_warp, int stride,
+                                            const float2 *xy_scan)
 {
     constexpr int SEG = 32 / APW;
     constexpr unsigned SEGMASK = SEG == 32 ? 0xffffffffu : ((1u << SEG) - 1u);
@@ -130,11 +157,8 @@ __device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &ro
     const int seg = lane / SEG, sl = lane % SEG, segbase = seg * SEG;
     const int a = a_first + seg;
     const bool real = a < a_end;
-    // instance fields in registers for the whole tour
     const int n = I.n, kp = I.k_pad, G = kp >> 2, kind = I.kind;
     const uint64_t seed = I.seed;
-    const double *__restrict__ cdist = I.cdist;
-    const int32_t *__restrict__ fbl = I.fbl;
     const float *__restrict__ cost = I.cost;
     const float2 *__restrict__ xy = xy_scan;   // coordinates for the fallback scan
     const int nwords = (n + 31) >> 5;
@@ -148,12 +172,12 @@ __device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &ro
     const int start = (int)__umulhi(__shfl_sync(FULL_MASK, rnd.x, segbase), (uint32_t)n);
     if (sl == 0 && real) vis[start >> 5] |= 1u << (start & 31);
     __syncwarp();
-    int tb = sl == 0 ? start : 0;
+    int tb = sl == 0 ? start : 0;                  // step s of the tour / slot at lane s % SEG
+    unsigned sb8 = 0xffu;
     int32_t *tour = I.tours + (size_t)(real ? a : 0) * n;
-    // L = ((d_1 + d_2) + ...) in step order; each d is added two steps after
-    // its load was issued, so the load latency never stalls the next step
-    double L = 0.0, dq1 = 0.0, dq2 = 0.0;
-    unsigned nfb = 0;
+    uint8_t *slots = I.slots + (size_t)(real ? a : 0) * n;
+    int32_t *fbs = I.fbs + (size_t)(real ? a : 0) * n;
+    int nfb = 0;
     int cur = start;
     // the row of the current node is loaded at the end of the previous step
     int4 id = make_int4(-1, -1, -1, -1);
@@ -161,6 +185,14 @@ __device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &ro
     if (real && sl < G) rows.load(cur, sl, id, ch);
 
     for (int s = 1; s < n; ++s) {
+        // draw s first: independent of the row, its shuffle overlaps the checks
+        const uint32_t q = (uint32_t)s >> 2;
+        if (q >= qbase + SEG) {
+            qbase += SEG;
+            rnd = draw_block(seed, (uint32_t)t, (uint32_t)(real ? a : 0), qbase + sl);
+        }
+        const uint32_t x = __shfl_sync(FULL_MASK, word_of(rnd, s & 3), (int)(q - qbase), SEG);
+
         auto unv = [&](int j) { return j >= 0 && !((vis[j >> 5] >> (j & 31)) & 1u); };
         const float w0 = unv(id.x) ? ch.x : 0.0f;
         const float w1 = unv(id.y) ? ch.y : 0.0f;
@@ -180,17 +212,6 @@ __device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &ro
         const float S2 = g0 ? p2 : __fadd_rn(ex, p2);
         const float S3 = g0 ? p3 : __fadd_rn(ex, p3);
         const float total = __shfl_sync(FULL_MASK, inc, 7, SEG);
-
-        const bool anyw = (w0 > 0.0f) | (w1 > 0.0f) | (w2 > 0.0f) | (w3 > 0.0f);
-        const unsigned live_bits = (__ballot_sync(FULL_MASK, anyw) >> segbase) & SEGMASK;
-        const bool live = live_bits != 0u || !real;
-
-        const uint32_t q = (uint32_t)s >> 2;
-        if (q >= qbase + SEG) {
-            qbase += SEG;
-            rnd = draw_block(seed, (uint32_t)t, (uint32_t)(real ? a : 0), qbase + sl);
-        }
-        const uint32_t x = __shfl_sync(FULL_MASK, word_of(rnd, s & 3), (int)(q - qbase), SEG);
         const float r = __fmul_rn(unif24(x), total);
 
         int hq = -1;
@@ -198,26 +219,45 @@ __device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &ro
         if (w2 > 0.0f && r < S2) hq = 2;
         if (w1 > 0.0f && r < S1) hq = 1;
         if (w0 > 0.0f && r < S0) hq = 0;
-        const unsigned hit_bits = (__ballot_sync(FULL_MASK, hq >= 0) >> segbase) & SEGMASK;
-        const int lastq = w3 > 0.0f ? 3 : w2 > 0.0f ? 2 : w1 > 0.0f ? 1 : 0;
-        const int src = hit_bits ? __ffs(hit_bits) - 1 : 31 - __clz(live_bits | 1u);
-        const int myq = hit_bits ? (hq < 0 ? 0 : hq) : lastq;
+        // an idle segment (no ant) counts as decided
+        const unsigned hit_all = __ballot_sync(FULL_MASK, hq >= 0 || (!real && sl == 0));
+        const unsigned hit_bits = (hit_all >> segbase) & SEGMASK;
+        // segments without a hit (no live slot, or the rounding corner case)
+        unsigned nohit = 0u;
+#pragma unroll
+        for (int g = 0; g < APW; ++g)
+            if (!((hit_all >> (g * SEG)) & SEGMASK)) nohit |= 1u << (g * SEG);
+        int src, myq;
+        bool live = true;
+        unsigned need = 0u;
+        if (!nohit) {                                   // common case: one ballot
+            src = __ffs(hit_bits) - 1;
+            myq = hq < 0 ? 0 : hq;
+        } else {
+            const bool anyw = (w0 > 0.0f) | (w1 > 0.0f) | (w2 > 0.0f) | (w3 > 0.0f);
+            const unsigned live_all = __ballot_sync(FULL_MASK, anyw);
+            const unsigned live_bits = (live_all >> segbase) & SEGMASK;
+            live = live_bits != 0u || !real;
+            const int lastq = w3 > 0.0f ? 3 : w2 > 0.0f ? 2 : w1 > 0.0f ? 1 : 0;
+            src = hit_bits ? __ffs(hit_bits) - 1 : 31 - __clz(live_bits | 1u);
+            myq = hit_bits ? (hq < 0 ? 0 : hq) : lastq;
+            need = __ballot_sync(FULL_MASK, sl == 0 && !live);
+        }
         // chosen node and slot in one shuffle: (node << 2) | slot-in-lane
         const int packed = __shfl_sync(FULL_MASK, (int)(((unsigned)int_of(id, myq) << 2) | (unsigned)myq),
                                        src, SEG);
         int nxt = packed >> 2;
-        const int cq = packed & 3;
+        unsigned slot = (unsigned)(src * 4 + (packed & 3));
 
         // ---- nearest unvisited node, one needing segment at a time, whole warp
-        unsigned need = __ballot_sync(FULL_MASK, sl == 0 && !live);
         while (need) {
             const int sb = __ffs(need) - 1;
             need &= need - 1u;
             const int scur = __shfl_sync(FULL_MASK, cur, sb);
             const unsigned *sv = vis_warp + (sb / SEG) * stride;
             int found = -1;
-            if (fbl) {
-                const int u = fbl[(size_t)scur * FBL + lane];
+            if (list.present()) {
+                const int u = list.get(scur, lane);
                 const bool ok = u >= 0 && !((sv[u >> 5] >> (u & 31)) & 1u);
                 const unsigned bm = __ballot_sync(FULL_MASK, ok);
                 if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
@@ -255,35 +295,29 @@ __device__ __forceinline__ unsigned build_tours(const DevInst &I, const Rows &ro
                 }
                 found = bu;
             }
-            if (segbase == sb) nxt = found;
+            if (segbase == sb) {
+                nxt = found;
+                slot = SLOT_FALLBACK;
+                if (sl == 0) fbs[nfb++] = s;
+            }
         }
         if ((unsigned)nxt >= (unsigned)n) nxt = 0;   // unreachable for finite keys; keeps indices in range
 
         // next row first, so its latency overlaps the bookkeeping below
         if (real && sl < G && s + 1 < n) rows.load(nxt, sl, id, ch);
-        if (sl == 0 && real) {
-            L = __dadd_rn(L, dq2);
-            dq2 = dq1;
-            if (!live) { dq1 = dist64(I, cur, nxt); ++nfb; }
-            else dq1 = cdist[(size_t)cur * kp + src * 4 + cq];
-            vis[nxt >> 5] |= 1u << (nxt & 31);
-        }
+        if (sl == 0 && real) vis[nxt >> 5] |= 1u << (nxt & 31);
         __syncwarp();
-        const int slot = s % SEG;
-        if (sl == slot) tb = nxt;
-        if (slot == SEG - 1 || s == n - 1) {
-            if (real && sl <= slot) tour[s - slot + sl] = tb;
+        const int ts = s % SEG;
+        if (sl == ts) { tb = nxt; sb8 = slot; }
+        if (ts == SEG - 1 || s == n - 1) {
+            if (real && sl <= ts) {
+                tour[s - ts + sl] = tb;
+                slots[s - ts + sl] = (uint8_t)sb8;
+            }
         }
         cur = nxt;
     }
-    if (sl == 0 && real) {
-        // the pipeline holds the last two edges (for n = 2 only one real edge)
-        L = __dadd_rn(L, dq2);
-        L = __dadd_rn(L, dq1);
-        L = __dadd_rn(L, dist64(I, cur, start));
-        I.lens[a] = L;
-    }
-    return nfb;
+    if (sl == 0 && real) I.fbcnt[a] = nfb;
 }
 
 }  // namespace hac

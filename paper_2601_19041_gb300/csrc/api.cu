@@ -55,7 +55,7 @@ int check_params(const hac_instance &in, const hac_params &p)
     if (in.kind == 0 && !in.coords) return HAC_EINVAL;
     if (in.kind == 1 && !in.cost) return HAC_EINVAL;
     if (!in.h_rowptr || (in.h_dtype != 0 && in.h_dtype != 1)) return HAC_EINVAL;
-    if (p.k < 1 || p.k > HAC_KMAX || p.m < 1 || p.iterations < 0) return HAC_EINVAL;
+    if (p.k < 1 || p.k > HAC_KMAX || p.m < 1 || p.m > HAC_MMAX || p.iterations < 0) return HAC_EINVAL;
     if (!(p.rho > 0.0 && p.rho < 1.0) || p.degree_target < 1) return HAC_EINVAL;
     if (!(p.alpha > 0.0) || !(p.beta >= 0.0) || !(p.theta_h >= 0.0) || !(p.eps > 0.0)) return HAC_EINVAL;
     if (!(p.q_level >= 0.0 && p.q_level <= 1.0) || !(p.p_best > 0.0 && p.p_best < 1.0)) return HAC_EINVAL;
@@ -167,6 +167,10 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
     put("succ", A.take(n * 4));
     put("pred", A.take(n * 4));
     put("tours", A.take((size_t)z.m * n * 4));
+    put("slots", A.take((size_t)z.m * n));
+    put("dstep", A.take((size_t)z.m * n * 8));
+    put("fbs", A.take((size_t)z.m * n * 4));
+    put("fbcnt", A.take((size_t)z.m * 4));
     put("lens", A.take((size_t)z.m * 8));
     put("trace", A.take((size_t)TRACE_W * std::max(z.iters, 1) * 8));
 }
@@ -226,7 +230,7 @@ int plan_batch(const hac_instance *ins, const hac_params *ps, int count, int on_
 
 struct FusedGroup {
     int clog = 0, count = 0, order_off = 0;
-    int rows_cap = 0, kp_cap = 0, stride = 0, warps = 0, xy_cap = 0;
+    int rows_cap = 0, kp_cap = 0, stride = 0, warps = 0, xy_cap = 0, list_rows = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
 };
@@ -247,7 +251,7 @@ struct hac_batch {
     int32_t *d_order = nullptr;
     std::vector<FusedGroup> groups;   // non-empty when the fused kernel is used
     int *d_err = nullptr;
-    int max_n = 0;
+    int max_n = 0, max_kp = 0;
     bool any_ls = false;
     std::vector<int> t_host;
     cudaGraphExec_t gexec = nullptr;
@@ -304,8 +308,8 @@ int fold_events(hac_batch *bt)
 // least 2^cluster_log2), each group ordered by decreasing work.
 static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
 {
-    const int apw = bt->ex.ants_per_warp == 2 ? 2 : 4;
-    bt->ex.ants_per_warp = apw;
+    const int apw = bt->ex.ants_per_warp == 2 ? 2 : bt->ex.ants_per_warp == 32 ? 32 : 4;
+    if (apw != bt->ex.ants_per_warp) return HAC_EUNSUPPORTED;   // the fused kernel has no 1-ant-per-warp form
     const int count = bt->count;
     std::vector<int> clog(count, -1);
     auto fits = [&](int b, int cl, int &rows, int &warps) {
@@ -315,7 +319,7 @@ static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
         const int apc = (z.m + C - 1) / C;
         warps = (apc + apw - 1) / apw;
         if (warps > 16) return false;   // k_fused is compiled for at most 512 threads
-        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 31) / 32, 0) <= FUSED_SMEM_LIMIT;
+        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 31) / 32, 0, 0) <= FUSED_SMEM_LIMIT;
     };
     for (int b = 0; b < count; ++b) {
         if (bt->zs[b].n > 65534) return HAC_EUNSUPPORTED;
@@ -341,7 +345,7 @@ static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
                 G.warps = std::max(G.warps, warps);
             }
             if (!G.count) continue;
-            const size_t base = fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, 0);
+            const size_t base = fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, 0, 0);
             if (base > FUSED_SMEM_LIMIT) {
                 if (cl == 3) return HAC_EUNSUPPORTED;
                 for (int b = 0; b < count; ++b) if (clog[b] == cl) clog[b] = cl + 1;
@@ -352,6 +356,11 @@ static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
             int nmax = 0;
             for (int b = 0; b < count; ++b) if (clog[b] == cl) nmax = std::max(nmax, bt->zs[b].n);
             if (base + (size_t)nmax * 8 <= FUSED_SMEM_LIMIT) G.xy_cap = nmax;
+            // and the lookup lists of this CTA's rows (lane kernel only)
+            if (bt->ex.fallback_list &&
+                fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, G.xy_cap, G.rows_cap) <=
+                    FUSED_SMEM_LIMIT)
+                G.list_rows = G.rows_cap;
             bt->groups.push_back(G);
         }
         if (!again) break;
@@ -444,7 +453,8 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     hac_exec_default(&ex);
     if (exec) ex = *exec;
     if (ex.ants_per_warp == 0) ex.ants_per_warp = 4;
-    if (ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4) return HAC_EINVAL;
+    if (ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 32)
+        return HAC_EINVAL;
     if (ex.warps_per_block == 0) ex.warps_per_block = 4;
     if (ex.warps_per_block < 1 || ex.warps_per_block > 8) return HAC_EINVAL;
     if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
@@ -512,7 +522,8 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
             SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
             SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *)
             SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
-            SETP(fbl, int32_t *)
+            SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)
+            SETP(fbcnt, int32_t *)
 #undef SETP
             if (!std::strcmp(name, "xy")) D.xy = (const float *)ptr;
             if (!std::strcmp(name, "cost")) D.cost = (const float *)ptr;
@@ -521,6 +532,8 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
             if (!std::strcmp(name, "val")) D.val = ptr;
         });
         if (!ex.fallback_list) D.fbl = nullptr;
+        if (ex.ants_per_warp == 32) { D.tour_sa = 1; D.tour_ss = p.m; }   // step-major tours
+        else { D.tour_sa = z.n; D.tour_ss = 1; }
         D.fbl_len = ex.fallback_list;
         if (!inputs_on_device) {
             const size_t n = z.n, nnz = (size_t)z.nnz;
@@ -534,6 +547,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
             }
         }
         bt->max_n = std::max(bt->max_n, z.n);
+        bt->max_kp = std::max(bt->max_kp, z.kp);
         bt->any_ls |= z.ls != 0;
     }
     // work tables
@@ -596,7 +610,7 @@ static int enqueue_iteration(hac_batch *bt)
 {
     int k = timed(bt, 0, [&] {
         return launch_construct(bt->d_inst, bt->d_warpmap, bt->warpmap_len, bt->ex.ants_per_warp,
-                                bt->ex.warps_per_block, bt->max_n, bt->stream);
+                                bt->ex.warps_per_block, bt->max_n, bt->max_kp, bt->count, bt->stream);
     });
     k += timed(bt, 1, [&] {
         return launch_iteration_tail(bt->d_inst, bt->count, bt->d_slotmap, bt->slotmap_len,
@@ -620,7 +634,7 @@ static int enqueue_fused(hac_batch *bt, int iters)
             const FusedGroup &G = bt->groups[g];
             cudaError_t e = launch_fused(bt->d_inst, bt->d_order + G.order_off, G.count, G.clog,
                                          bt->ex.ants_per_warp, G.warps, G.rows_cap, G.kp_cap,
-                                         G.stride, G.xy_cap, iters, g ? G.side : s);
+                                         G.stride, G.xy_cap, G.list_rows, iters, g ? G.side : s);
             if (e != cudaSuccess && err == cudaSuccess) err = e;
         }
         for (size_t g = 1; g < bt->groups.size(); ++g) {
@@ -711,7 +725,17 @@ int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size
     case HAC_F_NN_TOUR: src = D.nn_tour; sz = n * 4; break;
     case HAC_F_GB_TOUR: src = D.gb_tour; sz = n * 4; break;
     case HAC_F_IB_TOUR: src = D.ib_tour; sz = n * 4; break;
-    case HAC_F_TOURS: src = D.tours; sz = m * n * 4; break;
+    case HAC_F_TOURS:
+        if (D.tour_ss != 1) {   // step-major on the device: transpose into ant-major
+            if (bytes < m * n * 4) return HAC_EINVAL;
+            std::vector<int32_t> tmp(m * n);
+            CK(cudaMemcpy(tmp.data(), D.tours, m * n * 4, cudaMemcpyDeviceToHost));
+            int32_t *o = (int32_t *)host_dst;
+            for (size_t a = 0; a < m; ++a)
+                for (size_t q = 0; q < n; ++q) o[a * n + q] = tmp[q * m + a];
+            return HAC_OK;
+        }
+        src = D.tours; sz = m * n * 4; break;
     case HAC_F_LENS: src = D.lens; sz = m * 8; break;
     case HAC_F_NBR:
         if (!D.ls_k) return HAC_EINVAL;

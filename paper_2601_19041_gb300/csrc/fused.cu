@@ -17,7 +17,7 @@
 // per-iteration kernels (ant.cuh, iter.cuh, twoopt.cuh).
 #include <cooperative_groups.h>
 
-#include "ant.cuh"
+#include "ant_lane.cuh"
 #include "iter.cuh"
 #include "twoopt.cuh"
 
@@ -35,6 +35,7 @@ struct FusedArgs {
     int warps;                // warps per CTA
     int apw;
     int xy_cap;               // nodes whose coordinates fit in shared memory (0: read from global)
+    int list_rows;            // lookup-list rows per CTA in shared memory (0: lists from global)
 };
 
 __host__ __device__ inline size_t fused_table_bytes(int rows_cap, int kp_cap)
@@ -44,11 +45,14 @@ __host__ __device__ inline size_t fused_table_bytes(int rows_cap, int kp_cap)
     return ch + ix;
 }
 
-template <int APW, int CLOG>
+// APW ants per warp: 2 or 4 (warp segments, ant.cuh) or 32 (one ant per lane,
+// ant_lane.cuh, NG candidate groups).  Shared memory per CTA:
+//   choice rows (FP32) | candidate ids (uint16) | visited masks |
+//   coordinates (optional) | lookup lists (uint16, optional)
+template <int APW, int NG, int CLOG>
 __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
 {
     constexpr int C = 1 << CLOG;
-    constexpr int SEG = 32 / APW;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int cid = blockIdx.x >> CLOG;
@@ -59,7 +63,8 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
     uint16_t *sidx = reinterpret_cast<uint16_t *>(smem + (size_t)A.rows_cap * A.kp_cap * 4);
     unsigned *svis = reinterpret_cast<unsigned *>(smem + fused_table_bytes(A.rows_cap, A.kp_cap));
     float2 *sxy = reinterpret_cast<float2 *>(smem + fused_table_bytes(A.rows_cap, A.kp_cap) +
-                                             (size_t)A.warps * A.apw * A.stride * 4);
+                                             (size_t)A.warps * APW * A.stride * 4);
+    uint16_t *slist = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(sxy) + (size_t)A.xy_cap * 8);
 
     const int n = I.n, kp = I.k_pad, m = I.m;
     const int R = (n + C - 1) >> CLOG;   // local rows: i = rank + C*l
@@ -81,10 +86,20 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
     if (xy_shared)
         for (int e = threadIdx.x; e < n; e += blockDim.x) sxy[e] = reinterpret_cast<const float2 *>(I.xy)[e];
     const float2 *xy_scan = xy_shared ? sxy : reinterpret_cast<const float2 *>(I.xy);
+    const bool list_shared = I.fbl != nullptr && A.list_rows >= R;
+    if (list_shared)
+        for (int e = threadIdx.x; e < R * FBL; e += blockDim.x) {
+            const int l = e / FBL, k = e - l * FBL;
+            const int i = rank + (l << CLOG);
+            const int v = i < n ? I.fbl[(size_t)i * FBL + k] : -1;
+            slist[e] = v < 0 ? (uint16_t)0xffff : (uint16_t)v;
+        }
     ClusterRows<CLOG> rows;
     rows.idx_base = (uint32_t)__cvta_generic_to_shared(sidx);
     rows.ch_base = (uint32_t)__cvta_generic_to_shared(sch);
     rows.kp = kp;
+    const ClusterList<CLOG> clist{list_shared ? (uint32_t)__cvta_generic_to_shared(slist) : 0u};
+    const GlobalList glist{I.fbl};
     const int t0 = st->t;
     cl.sync();
 
@@ -92,14 +107,22 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
     const int apc = (m + C - 1) >> CLOG;   // ants per CTA
     const int a_lo = rank * apc, a_hi = min(m, a_lo + apc);
     const float omega = __double2float_rn(__dsub_rn(1.0, I.rho));
+    unsigned *vis_w = svis + (size_t)wib * APW * A.stride;
 
     for (int t = t0; t < t_end; ++t) {
         const int a_first = a_lo + wib * APW;
         if (a_first < a_hi) {
-            const unsigned nfb = build_tours<APW>(I, rows, t, a_first, a_hi,
-                                                  svis + (size_t)wib * APW * A.stride, A.stride, xy_scan);
-            if (lane % SEG == 0 && nfb) atomicAdd(&st->n_fallback, (unsigned long long)nfb);
+            if constexpr (APW == 32) {
+                if (list_shared) build_tours_lane<NG>(I, rows, clist, t, a_first, a_hi, vis_w, xy_scan);
+                else build_tours_lane<NG>(I, rows, glist, t, a_first, a_hi, vis_w, xy_scan);
+            } else {
+                if (list_shared) build_tours<APW>(I, rows, clist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
+                else build_tours<APW>(I, rows, glist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
+            }
         }
+        __syncthreads();
+        fallback_distances(I, a_lo, a_hi);     // this CTA's ants only: no cluster barrier needed
+        ant_lengths(I, a_lo, a_hi);
         __threadfence();
         cl.sync();
         if (rank == 0) {
@@ -137,21 +160,20 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
 
 // ------------------------------------------------------------ host side
 
-template <int APW, int CLOG>
-static cudaError_t launch_fused_t(const FusedArgs &A, int clusters, int warps, size_t smem,
-                                  cudaStream_t s)
+template <typename Kern>
+static cudaError_t launch_cluster(Kern kern, int clog, const FusedArgs &A, int clusters, int warps,
+                                  size_t smem, cudaStream_t s)
 {
-    auto kern = k_fused<APW, CLOG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(clusters << CLOG), 1, 1);
+    cfg.gridDim = dim3((unsigned)(clusters << clog), 1, 1);
     cfg.blockDim = dim3((unsigned)(warps * 32), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 1 << CLOG;
+    attr[0].val.clusterDim.x = 1 << clog;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -159,31 +181,34 @@ static cudaError_t launch_fused_t(const FusedArgs &A, int clusters, int warps, s
     return cudaLaunchKernelEx(&cfg, kern, A);
 }
 
-size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap)
+size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap,
+                        int list_rows)
 {
-    return fused_table_bytes(rows_cap, kp_cap) + (size_t)warps * apw * stride * 4 + (size_t)xy_cap * 8;
+    return fused_table_bytes(rows_cap, kp_cap) + (size_t)warps * apw * stride * 4 + (size_t)xy_cap * 8 +
+           (size_t)list_rows * FBL * 2;
 }
 
 cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, int clusters, int clog,
                          int apw, int warps, int rows_cap, int kp_cap, int stride, int xy_cap,
-                         int iters, cudaStream_t s)
+                         int list_rows, int iters, cudaStream_t s)
 {
-    FusedArgs A{d_inst, d_order, iters, rows_cap, kp_cap, stride, warps, apw, xy_cap};
-    const size_t smem = fused_smem_bytes(rows_cap, kp_cap, warps, apw, stride, xy_cap);
-    if (apw == 2) {
-        switch (clog) {
-        case 0: return launch_fused_t<2, 0>(A, clusters, warps, smem, s);
-        case 1: return launch_fused_t<2, 1>(A, clusters, warps, smem, s);
-        case 2: return launch_fused_t<2, 2>(A, clusters, warps, smem, s);
-        default: return launch_fused_t<2, 3>(A, clusters, warps, smem, s);
-        }
+    FusedArgs A{d_inst, d_order, iters, rows_cap, kp_cap, stride, warps, apw, xy_cap, list_rows};
+    const size_t smem = fused_smem_bytes(rows_cap, kp_cap, warps, apw, stride, xy_cap, list_rows);
+#define CLUSTER_SWITCH(APWV, NGV) \
+    switch (clog) { \
+    case 0: return launch_cluster(k_fused<APWV, NGV, 0>, 0, A, clusters, warps, smem, s); \
+    case 1: return launch_cluster(k_fused<APWV, NGV, 1>, 1, A, clusters, warps, smem, s); \
+    case 2: return launch_cluster(k_fused<APWV, NGV, 2>, 2, A, clusters, warps, smem, s); \
+    default: return launch_cluster(k_fused<APWV, NGV, 3>, 3, A, clusters, warps, smem, s); }
+    if (apw == 32) {
+        const int G = kp_cap / 4;
+        if (G <= 3) { CLUSTER_SWITCH(32, 3) }
+        if (G <= 5) { CLUSTER_SWITCH(32, 5) }
+        CLUSTER_SWITCH(32, 8)
     }
-    switch (clog) {
-    case 0: return launch_fused_t<4, 0>(A, clusters, warps, smem, s);
-    case 1: return launch_fused_t<4, 1>(A, clusters, warps, smem, s);
-    case 2: return launch_fused_t<4, 2>(A, clusters, warps, smem, s);
-    default: return launch_fused_t<4, 3>(A, clusters, warps, smem, s);
-    }
+    if (apw == 2) { CLUSTER_SWITCH(2, 0) }
+    CLUSTER_SWITCH(4, 0)
+#undef CLUSTER_SWITCH
 }
 
 }  // namespace hac

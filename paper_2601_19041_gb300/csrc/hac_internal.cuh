@@ -28,6 +28,7 @@ struct InstState {
     int32_t active;     // 1 while the current iteration runs for this instance
     int32_t n_lambda;
     unsigned long long n_fallback;
+    int32_t fbl_unsafe; // 1: some choice value could reach 0, lookup lists keep the candidates
 };
 
 // Device view of one instance: sizes, parameters and pointers into the workspace.
@@ -62,7 +63,12 @@ struct DevInst {
     int32_t fbl_len;
     // search state
     int32_t *nn_tour, *gb_tour, *ib_tour, *succ, *pred;   // n each
-    int32_t *tours;           // m*n
+    int32_t *tours;           // m*n: tour of ant a, step s at a*tour_sa + s*tour_ss
+    int32_t tour_sa, tour_ss; // (n, 1) ant-major, or (1, m) step-major (one ant per lane)
+    uint8_t *slots;           // m*n chosen slot per step (same layout as tours), 0xff: nearest-unvisited
+    double *dstep;            // m*n d of the edge entering step s (same layout); s = 0: closing edge
+    int32_t *fbs;             // m*n nearest-unvisited steps of ant a at a*n + k
+    int32_t *fbcnt;           // m   their number in the current iteration
     double *lens;             // m
     double *trace;            // TRACE_W*iters
     InstState *st;
@@ -231,14 +237,15 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
                 int rowmap_len, const int2 *d_slotmap, int slotmap_len, int *d_err,
                 cudaStream_t s);
 int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
-                     int warps_per_block, int max_n, cudaStream_t s);
+                     int warps_per_block, int max_n, int max_kp, int count, cudaStream_t s);
 int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
                           int slotmap_len, bool any_ls, cudaStream_t s);
 // fused cluster kernel (fused.cu): one cluster of 2^clog CTAs per instance
-size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap);
+size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap,
+                        int list_rows);
 cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, int clusters, int clog,
                          int apw, int warps, int rows_cap, int kp_cap, int stride, int xy_cap,
-                         int iters, cudaStream_t s);
+                         int list_rows, int iters, cudaStream_t s);
 constexpr size_t FUSED_SMEM_LIMIT = 220 * 1024;   // dynamic shared memory per CTA we allow
 
 }  // namespace hac

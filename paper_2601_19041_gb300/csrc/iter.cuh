@@ -52,8 +52,8 @@ __device__ __forceinline__ int block_iteration_best(const DevInst &I, InstState 
     }
     __syncthreads();
     const int ib = ib_s;
-    const int32_t *src = I.tours + (size_t)ib * I.n;
-    for (int s = threadIdx.x; s < I.n; s += blockDim.x) I.ib_tour[s] = src[s];
+    const int32_t *src = I.tours + (size_t)ib * I.tour_sa;
+    for (int s = threadIdx.x; s < I.n; s += blockDim.x) I.ib_tour[s] = src[(size_t)s * I.tour_ss];
     __syncthreads();
     return ib;
 }

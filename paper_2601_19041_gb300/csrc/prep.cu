@@ -15,7 +15,7 @@
 // block per instance.
 #include <cuda_fp16.h>
 
-#include "hac_internal.cuh"
+#include "lengths.cuh"
 
 namespace hac {
 
@@ -649,26 +649,55 @@ __global__ void k_nbr(const DevInst *insts, const int2 *rowmap)
 
 // ------------------------------------------------------------ nearest-unvisited lookup lists
 
-// For the fallback of Alg. 2: the 32 nodes u != i with the smallest
-// (FP32 key, u), ascending (-1 when n-1 < 32).  If one of them is unvisited,
-// the first unvisited one is the nearest unvisited node, exactly.
-__global__ void k_fbl(const DevInst *insts, const int2 *rowmap)
+// The fallback of Alg. 2 happens when no candidate of the current node has a
+// positive weight.  When every candidate's choice value stays positive for
+// the whole run (alpha = 1 and fl32(tau_min * W) > 0 at the smallest bound,
+// which only grows), that means all candidates are visited, so the lookup
+// list may skip them.
+__global__ void k_fbl_check(const DevInst *insts, const int2 *slotmap)
 {
+    int2 sm = slotmap[blockIdx.x];
+    const DevInst &I = insts[sm.x];
+    if (!I.fbl) return;
+    size_t s = (size_t)sm.y + threadIdx.x;
+    if (s >= (size_t)I.n * I.k_pad) return;
+    if (I.alpha != 1.0) { if (s == 0) I.st->fbl_unsafe = 1; return; }
+    if (I.cand[s] >= 0 && !(__fmul_rn(I.st->tau_min, I.W[s]) > 0.0f)) I.st->fbl_unsafe = 1;
+}
+
+// For the fallback of Alg. 2: the 32 nodes u != i (not in C_i when that is
+// safe, see k_fbl_check) with the smallest (FP32 key, u), ascending, -1 when
+// fewer exist.  If one of them is unvisited at a fallback, the first unvisited
+// one is the nearest unvisited node, exactly.
+__global__ void k_fbl(const DevInst *insts, const int2 *rowmap, int words_per_warp)
+{
+    extern __shared__ unsigned int excl_mask[];
     int2 rm = rowmap[blockIdx.x];
     const DevInst &I = insts[rm.x];
     if (!I.fbl) return;
     const int i = rm.y + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (i >= I.n) return;
+    unsigned *mask = excl_mask + (size_t)(threadIdx.x / 32) * words_per_warp;
+    const int nw = (I.n + 31) >> 5;
+    for (int w = lane; w < nw; w += 32) mask[w] = 0u;
+    __syncwarp();
+    const bool excl = I.st->fbl_unsafe == 0;
+    if (excl && lane < I.k_pad) {
+        const int j = I.cand[(size_t)i * I.k_pad + lane];
+        if (j >= 0) atomicOr(&mask[j >> 5], 1u << (j & 31));
+    }
+    __syncwarp();
     const float2 *xy = reinterpret_cast<const float2 *>(I.xy);
     const float2 pi = I.kind == 0 ? xy[i] : make_float2(0.f, 0.f);
-    const int K = I.n - 1 < 32 ? I.n - 1 : 32;
+    const int avail = I.n - 1 - (excl ? I.k_eff : 0);
+    const int K = avail < 32 ? avail : 32;
     float pk = -1.0f;
     int pu = -1, mine = -1;
     for (int r = 0; r < K; ++r) {
         float bk = __int_as_float(0x7f800000);
         int bu = 0x7fffffff;
         for (int u = lane; u < I.n; u += 32) {
-            if (u == i) continue;
+            if (u == i || ((mask[u >> 5] >> (u & 31)) & 1u)) continue;
             const float kk = I.kind == 0 ? key32_xy(pi, xy[u]) : I.cost[(size_t)i * I.n + u];
             if (key_less(pk, pu, kk, u) && key_less(kk, u, bk, bu)) { bk = kk; bu = u; }
         }
@@ -683,8 +712,7 @@ __global__ void k_fbl(const DevInst *insts, const int2 *rowmap)
 // ------------------------------------------------------------ T_NN
 
 // Nearest-neighbour tour from node 0 (one block per instance): each step takes
-// the unvisited node of smallest (FP32 key, index); L_nn is summed in FP64 in
-// tour order by thread 0.
+// the unvisited node of smallest (FP32 key, index); then L_nn.
 __global__ void k_nn_tour(const DevInst *insts)
 {
     const DevInst &I = insts[blockIdx.x];
@@ -699,7 +727,6 @@ __global__ void k_nn_tour(const DevInst *insts)
     __syncthreads();
     const float2 *xy = reinterpret_cast<const float2 *>(I.xy);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    double L = 0.0;
     int cur = 0;
     for (int s = 1; s < n; ++s) {
         float2 pc = I.kind == 0 ? xy[cur] : make_float2(0.f, 0.f);
@@ -721,14 +748,17 @@ __global__ void k_nn_tour(const DevInst *insts)
                 if ((unsigned)bu >= (unsigned)n) bu = 0;   // unreachable for finite keys
                 vis[bu >> 5] |= 1u << (bu & 31);
                 I.nn_tour[s] = bu;
-                L = __dadd_rn(L, dist64(I, cur, bu));
                 cur_s = bu;
             }
         }
         __syncthreads();
         cur = cur_s;
     }
-    if (threadIdx.x == 0) I.st->L_nn = __dadd_rn(L, dist64(I, cur, 0));
+    __syncthreads();
+    if (wid == 0) {   // eq. (tour_length) in the blocked pairwise order
+        const double Ln = warp_tour_length(I, I.nn_tour);
+        if (lane == 0) I.st->L_nn = Ln;
+    }
 }
 
 // ------------------------------------------------------------ bounds and tau
@@ -808,15 +838,20 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
     k_evidence<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
     k_kappa<<<count, 1024, 0, s>>>(d_inst);
     k_weights<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
-    k_fbl<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap);
-    launched += 6;
+    launched += 5;
     if (any_ls) { k_nbr<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap); ++launched; }
     size_t vis_bytes = (size_t)((max_n + 31) / 32) * 4;
     k_nn_tour<<<count, 1024, vis_bytes, s>>>(d_inst);
     if (any_ls) { launch_two_opt_nn(d_inst, count, s); ++launched; }
     k_init_bounds<<<count, 256, 0, s>>>(d_inst);
+    k_fbl_check<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
+    const int wpw = (max_n + 31) / 32;
+    const size_t fbl_smem = (size_t)ROW_WARPS * wpw * sizeof(unsigned);
+    if (fbl_smem > 48 * 1024)
+        cudaFuncSetAttribute(k_fbl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbl_smem);
+    k_fbl<<<rowmap_len, threads, fbl_smem, s>>>(d_inst, d_rowmap, wpw);
     k_init_tau<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
-    return launched + 3;
+    return launched + 5;
 }
 
 }  // namespace hac

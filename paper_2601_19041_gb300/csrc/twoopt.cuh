@@ -22,7 +22,7 @@
 //   kernel always terminates.
 #pragma once
 
-#include "hac_internal.cuh"
+#include "lengths.cuh"
 
 namespace hac {
 
@@ -130,22 +130,6 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
             }
         }
     } while (round_moves > 0 && moves < max_moves);
-}
-
-// eq. (tour_length) in FP64: edge lengths in parallel, summed in tour order
-__device__ __forceinline__ double warp_tour_length(const DevInst &I, const int32_t *tour)
-{
-    const int lane = threadIdx.x & 31, n = I.n;
-    double L = 0.0;
-    for (int base = 1; base < n; base += 32) {
-        const int s = base + lane;
-        const double d = s < n ? dist64(I, tour[s - 1], tour[s]) : 0.0;
-        for (int l = 0; l < 32 && base + l < n; ++l) {
-            const double dl = __shfl_sync(FULL2, d, l);
-            L = __dadd_rn(L, dl);
-        }
-    }
-    return __dadd_rn(L, dist64(I, tour[n - 1], tour[0]));
 }
 
 }  // namespace hac

@@ -111,7 +111,8 @@ def test_case_parity(hac, orc, name):
     run_case(hac, orc, [inst], [p])
 
 
-@pytest.mark.parametrize("apw,wpb,graph,fbl", [(1, 4, 1, 0), (2, 8, 0, 32), (4, 2, 1, 32), (4, 8, 0, 0)])
+@pytest.mark.parametrize("apw,wpb,graph,fbl", [(1, 4, 1, 0), (2, 8, 0, 32), (4, 2, 1, 32), (4, 8, 0, 0),
+                                              (32, 4, 1, 32), (32, 2, 0, 0)])
 def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph, fbl):
     inst = synth.euclid_instance(31, 410, K=50)
     p = params(m=21, k=20, iterations=23, rho=0.2, seed=3)
@@ -119,7 +120,7 @@ def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph, fbl):
 
 
 FUSED = [dict(apw=2, clog=0, fbl=32), dict(apw=4, clog=1, fbl=0), dict(apw=4, clog=3, fbl=32),
-         dict(apw=2, clog=2, fbl=32)]
+         dict(apw=2, clog=2, fbl=32), dict(apw=32, clog=0, fbl=32), dict(apw=32, clog=2, fbl=0)]
 
 
 @pytest.mark.parametrize("cfg", FUSED, ids=lambda c: f"apw{c['apw']}_C{1 << c['clog']}_fbl{c['fbl']}")
@@ -138,6 +139,8 @@ def test_fused_mixed_batch_groups(hac, orc):
         insts.append(synth.euclid_instance(70 + b, n, K=20))
         ps.append(params(m=m, k=k, iterations=3 + b, rho=0.2, seed=170 + b))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(4, 0, 1, fused=1, fallback_list=32))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(32, 0, 1, fused=1, fallback_list=32))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(32, 4, 1, fused=0, fallback_list=32))
 
 
 def test_mixed_batch_parity(hac, orc):
