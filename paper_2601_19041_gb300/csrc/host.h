@@ -1,0 +1,404 @@
+// Host-side helpers shared by the batch API (api.cu) and the server
+// (serve.cu): input checks, the workspace layout of one instance, and the
+// grouping of instances for the fused cluster kernel.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hac_internal.cuh"
+
+namespace hac {
+namespace host {
+
+extern thread_local int g_last_cuda;
+
+#define CK(x)                                              \
+    do {                                                   \
+        cudaError_t e_ = (x);                              \
+        if (e_ != cudaSuccess) {                           \
+            g_last_cuda = (int)e_;                         \
+            return HAC_ECUDA;                              \
+        }                                                  \
+    } while (0)
+
+constexpr int ROWS_PER_BLOCK = 8;      // matches the row kernels (8 warps, a row each)
+constexpr int SLOTS_PER_BLOCK = 1024;  // matches the slot kernels
+constexpr int GRAPH_CHUNK = 10;        // iterations per captured graph
+constexpr int FBL_LEN = 32;            // nearest-unvisited lookup list (ant.cuh FBL)
+
+struct Arena {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        off = (off + 255) & ~(size_t)255;
+        size_t o = off;
+        off += bytes;
+        return o;
+    }
+};
+
+struct Sizes {
+    int n, kind, kp, k_eff, m, iters, ls, ls_k, sym, half;
+    long long nnz;
+};
+
+inline bool finite_f(float x) { return std::isfinite(x); }
+
+inline int check_params(const hac_instance &in, const hac_params &p)
+{
+    if (in.n < 3 || in.n > HAC_NMAX) return HAC_EINVAL;
+    if (in.kind != 0 && in.kind != 1) return HAC_EINVAL;
+    if (in.kind == 0 && !in.coords) return HAC_EINVAL;
+    if (in.kind == 1 && !in.cost) return HAC_EINVAL;
+    if (!in.h_rowptr || (in.h_dtype != 0 && in.h_dtype != 1)) return HAC_EINVAL;
+    if (p.k < 1 || p.k > HAC_KMAX || p.m < 1 || p.m > HAC_MMAX || p.iterations < 0) return HAC_EINVAL;
+    if (!(p.rho > 0.0 && p.rho < 1.0) || p.degree_target < 1) return HAC_EINVAL;
+    if (!(p.alpha > 0.0) || !(p.beta >= 0.0) || !(p.theta_h >= 0.0) || !(p.eps > 0.0)) return HAC_EINVAL;
+    if (!(p.q_level >= 0.0 && p.q_level <= 1.0) || !(p.p_best > 0.0 && p.p_best < 1.0)) return HAC_EINVAL;
+    if (!(p.c_cap >= 0.0) || !(p.logw_clip > 0.0)) return HAC_EINVAL;
+    if (p.baseline_scope != 0 && p.baseline_scope != 1) return HAC_EINVAL;
+    if (p.local_search != 0 && p.local_search != 1) return HAC_EINVAL;
+    if (p.local_search) {
+        if (in.kind != 0) return HAC_EUNSUPPORTED;
+        if (p.ls_k < 1 || p.ls_k > 32 || p.ls_k > in.n - 1) return HAC_EINVAL;
+    }
+    if (in.symmetrize != 0 && in.symmetrize != 1) return HAC_EINVAL;
+    return HAC_OK;
+}
+
+// full check of host-resident inputs (device inputs are checked by a kernel)
+inline int check_host_data(const hac_instance &in)
+{
+    const int n = in.n;
+    if (in.h_rowptr[0] != 0) return HAC_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        int b = in.h_rowptr[i], e = in.h_rowptr[i + 1];
+        if (e < b) return HAC_EINVAL;
+        for (int q = b; q < e; ++q) {
+            int j = in.h_col[q];
+            if (j < 0 || j >= n || j == i) return HAC_EINVAL;
+            if (q > b && in.h_col[q - 1] >= j) return HAC_EINVAL;
+            double v;
+            if (in.h_dtype == 1) {
+                uint16_t hb = ((const uint16_t *)in.h_val)[q];
+                int ex = (hb >> 10) & 31;
+                if (ex == 31) return HAC_EINVAL;
+                v = (hb >> 15) ? -1.0 : std::ldexp((double)(ex ? ((hb & 1023) | 1024) : (hb & 1023)),
+                                                   ex ? ex - 25 : -24);
+            } else {
+                v = ((const float *)in.h_val)[q];
+            }
+            if (!(v >= 0.0 && v <= 1.0)) return HAC_EINVAL;
+        }
+    }
+    if (in.kind == 0) {
+        for (long long q = 0; q < 2LL * n; ++q) if (!finite_f(in.coords[q])) return HAC_EINVAL;
+    } else {
+        for (long long q = 0; q < (long long)n * n; ++q) if (!finite_f(in.cost[q])) return HAC_EINVAL;
+    }
+    return HAC_OK;
+}
+
+inline int instance_sizes(const hac_instance &in, const hac_params &p, int on_dev, Sizes &z)
+{
+    int st = check_params(in, p);
+    if (st) return st;
+    z.n = in.n;
+    z.kind = in.kind;
+    z.kp = 4 * ((p.k + 3) / 4);
+    z.k_eff = std::min(p.k, in.n - 1);
+    z.m = p.m;
+    z.iters = p.iterations;
+    z.ls = p.local_search;
+    z.ls_k = p.local_search ? p.ls_k : 0;
+    z.sym = in.symmetrize;
+    z.half = in.h_dtype;
+    const long long last = in.h_nnz;
+    if (last < 0 || last > (1LL << 31) - 1) return HAC_EINVAL;
+    if (!on_dev && in.h_rowptr[in.n] != last) return HAC_EINVAL;
+    if (last > 0 && (!in.h_col || !in.h_val)) return HAC_EINVAL;
+    z.nnz = last;
+    return HAC_OK;
+}
+
+// Replays the same sequence of slices for sizing and for binding pointers.
+template <typename F>
+void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
+{
+    const size_t n = z.n, S = n * z.kp, nnz = (size_t)z.nnz;
+    const size_t cap = nnz + (z.sym ? nnz : 0);
+    if (!on_dev) {
+        if (z.kind == 0) put("xy", A.take(n * 8));
+        else put("cost", A.take(n * n * 4));
+        put("rowptr", A.take((n + 1) * 4));
+        put("col", A.take(nnz * 4 + 4));
+        put("val", A.take(nnz * (z.half ? 2 : 4) + 4));
+    }
+    if (z.sym) {
+        put("tcol", A.take(nnz * 4 + 4));
+        put("tval", A.take(nnz * 8 + 8));
+    }
+    put("mem_j", A.take(cap * 4 + 4));
+    put("mem_h", A.take(cap * 8 + 8));
+    put("mem_cnt", A.take(n * 4));
+    put("cand", A.take(S * 4));
+    put("cdist", A.take(S * 8));
+    put("conf", A.take(S * 8));
+    put("evid", A.take(S * 8));
+    put("logev", A.take(S * 8));
+    put("base", A.take(n * 8));
+    put("W", A.take(S * 4));
+    put("tau", A.take(S * 4));
+    put("choice", A.take(S * 4));
+    if (z.ls) {
+        put("nbr", A.take(n * z.ls_k * 4));
+        put("nbrd", A.take(n * z.ls_k * 8));
+        put("ls_pos", A.take(n * 4));
+        put("ls_dlb", A.take(n));
+    }
+    put("fbl", A.take(n * FBL_LEN * 4));
+    put("nn_tour", A.take(n * 4));
+    put("gb_tour", A.take(n * 4));
+    put("ib_tour", A.take(n * 4));
+    put("succ", A.take(n * 4));
+    put("pred", A.take(n * 4));
+    put("tours", A.take((size_t)z.m * n * 4));
+    put("slots", A.take((size_t)z.m * n));
+    put("dstep", A.take((size_t)z.m * n * 8));
+    put("fbs", A.take((size_t)z.m * n * 4));
+    put("fbcnt", A.take((size_t)z.m * 4));
+    put("lens", A.take((size_t)z.m * 8));
+    put("trace", A.take((size_t)TRACE_W * std::max(z.iters, 1) * 8));
+}
+
+// zero-initialised part: states, transpose counters, error word
+template <typename F>
+void layout_zero(Arena &A, const Sizes &z, F &&put)
+{
+    put("st", A.take(sizeof(InstState)));
+    if (z.sym) {
+        put("trowptr", A.take(((size_t)z.n + 1) * 4));
+        put("tfill", A.take((size_t)z.n * 4));
+    }
+}
+
+inline size_t map_sizes(const std::vector<Sizes> &zs, size_t &rows, size_t &slots, size_t &warps)
+{
+    rows = slots = warps = 0;
+    for (const Sizes &z : zs) {
+        rows += (z.n + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
+        slots += ((size_t)z.n * z.kp + SLOTS_PER_BLOCK - 1) / SLOTS_PER_BLOCK;
+        warps += z.m;   // bound for one ant per warp
+    }
+    return rows;
+}
+
+struct Plan {
+    std::vector<Sizes> zs;
+    size_t zero_bytes = 0, total = 0;
+};
+
+inline int plan_batch(const hac_instance *ins, const hac_params *ps, int count, int on_dev, Plan &P)
+{
+    if (!ins || !ps || count < 1) return HAC_EINVAL;
+    P.zs.resize(count);
+    for (int b = 0; b < count; ++b) {
+        int st = instance_sizes(ins[b], ps[b], on_dev, P.zs[b]);
+        if (st) return st;
+    }
+    Arena A;
+    A.take((size_t)count * sizeof(DevInst));
+    size_t rows, slots, warps;
+    map_sizes(P.zs, rows, slots, warps);
+    A.take(rows * sizeof(int2));
+    A.take(slots * sizeof(int2));
+    A.take(warps * sizeof(int4));
+    A.take((size_t)count * sizeof(int32_t));   // fused-kernel cluster -> instance order
+    size_t z0 = A.take(sizeof(int));       // error word starts the zero region
+    for (const Sizes &z : P.zs) layout_zero(A, z, [](const char *, size_t) {});
+    P.zero_bytes = A.off - z0;
+    for (const Sizes &z : P.zs) layout_instance(A, z, on_dev, [](const char *, size_t) {});
+    P.total = A.off + 256;
+    return HAC_OK;
+}
+
+
+struct FusedGroup {
+    int clog = 0, count = 0, order_off = 0;
+    int rows_cap = 0, kp_cap = 0, stride = 0, warps = 0, xy_cap = 0, list_rows = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+// pointers of the zero-initialised part of one instance
+inline void bind_zero(DevInst &D, const Sizes &z, Arena &A, char *B)
+{
+    layout_zero(A, z, [&](const char *name, size_t off) {
+        if (!std::strcmp(name, "st")) D.st = (InstState *)(B + off);
+        else if (!std::strcmp(name, "trowptr")) D.trowptr = (int32_t *)(B + off);
+        else if (!std::strcmp(name, "tfill")) D.tfill = (int32_t *)(B + off);
+    });
+}
+
+// sizes, parameters and workspace pointers of one instance
+inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &p, const Sizes &z,
+                          int inputs_on_device, const hac_exec &ex, Arena &A, char *B)
+{
+    D.n = z.n; D.kind = z.kind; D.k = p.k; D.k_eff = z.k_eff; D.k_pad = z.kp;
+    D.m = p.m; D.iters = p.iterations; D.ls_k = z.ls_k;
+    D.degree_target = p.degree_target; D.local_search = p.local_search;
+    D.baseline_scope = p.baseline_scope; D.symmetrize = in.symmetrize; D.h_half = in.h_dtype;
+    D.seed = p.seed;
+    D.nnz = (int32_t)z.nnz;
+    D.alpha = p.alpha; D.beta = p.beta; D.rho = p.rho; D.theta_h = p.theta_h; D.eps = p.eps;
+    D.c_cap = p.c_cap; D.q_level = p.q_level; D.p_best = p.p_best; D.logw_clip = p.logw_clip;
+    if (inputs_on_device) {
+        D.xy = in.coords; D.cost = in.cost; D.rowptr = in.h_rowptr; D.col = in.h_col;
+        D.val = in.h_val;
+    }
+    layout_instance(A, z, inputs_on_device, [&](const char *name, size_t off) {
+        void *ptr = B + off;
+#define SETP(f, T) if (!std::strcmp(name, #f)) D.f = (T)ptr;
+        SETP(tcol, int32_t *) SETP(tval, double *) SETP(mem_j, int32_t *) SETP(mem_h, double *)
+        SETP(mem_cnt, int32_t *) SETP(cand, int32_t *) SETP(cdist, double *) SETP(conf, double *)
+        SETP(evid, double *) SETP(logev, double *) SETP(base, double *) SETP(W, float *)
+        SETP(tau, float *) SETP(choice, float *) SETP(nbr, int32_t *) SETP(nbrd, double *)
+        SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
+        SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *)
+        SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
+        SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)
+        SETP(fbcnt, int32_t *)
+#undef SETP
+        if (!std::strcmp(name, "xy")) D.xy = (const float *)ptr;
+        if (!std::strcmp(name, "cost")) D.cost = (const float *)ptr;
+        if (!std::strcmp(name, "rowptr")) D.rowptr = (const int32_t *)ptr;
+        if (!std::strcmp(name, "col")) D.col = (const int32_t *)ptr;
+        if (!std::strcmp(name, "val")) D.val = ptr;
+    });
+    if (!ex.fallback_list) D.fbl = nullptr;
+    if (ex.ants_per_warp == 32) { D.tour_sa = 1; D.tour_ss = p.m; }   // step-major tours
+    else { D.tour_sa = z.n; D.tour_ss = 1; }
+    D.fbl_len = ex.fallback_list;
+}
+
+// host -> device copies of one instance's inputs into its workspace slices
+inline int upload_inputs(const DevInst &D, const hac_instance &in, const Sizes &z, cudaStream_t s)
+{
+    const size_t n = z.n, nnz = (size_t)z.nnz;
+    if (z.kind == 0) CK(cudaMemcpyAsync((void *)D.xy, in.coords, n * 8, cudaMemcpyHostToDevice, s));
+    else CK(cudaMemcpyAsync((void *)D.cost, in.cost, n * n * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void *)D.rowptr, in.h_rowptr, (n + 1) * 4, cudaMemcpyHostToDevice, s));
+    if (nnz) {
+        CK(cudaMemcpyAsync((void *)D.col, in.h_col, nnz * 4, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync((void *)D.val, in.h_val, nnz * (z.half ? 2 : 4), cudaMemcpyHostToDevice, s));
+    }
+    return HAC_OK;
+}
+
+// Groups the given instances by cluster size (the fewest CTAs whose shared
+// memory holds the instance's share of the candidate table and visited masks,
+// at least 2^clog_min), each group ordered by decreasing work.  `order` lists
+// instance indices group after group.
+inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &members, int apw,
+                       int clog_min, int fallback_list, std::vector<FusedGroup> &groups,
+                       std::vector<int32_t> &order)
+{
+    const int count = (int)members.size();
+    std::vector<int> clog(count, -1);
+    auto fits = [&](int q, int cl, int &rows, int &warps) {
+        const Sizes &z = zs[members[q]];
+        const int C = 1 << cl;
+        rows = (z.n + C - 1) / C;
+        const int apc = (z.m + C - 1) / C;
+        warps = (apc + apw - 1) / apw;
+        if (warps > 16) return false;   // k_fused is compiled for at most 512 threads
+        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 31) / 32, 0, 0) <= FUSED_SMEM_LIMIT;
+    };
+    for (int q = 0; q < count; ++q) {
+        if (zs[members[q]].n > 65534) return HAC_EUNSUPPORTED;
+        int rows, warps;
+        for (int cl = clog_min; cl <= 3; ++cl)
+            if (fits(q, cl, rows, warps)) { clog[q] = cl; break; }
+        if (clog[q] < 0) return HAC_EUNSUPPORTED;
+    }
+    for (;;) {   // group caps may exceed the limit when members differ: move a group up
+        groups.clear();
+        bool again = false;
+        for (int cl = 0; cl <= 3 && !again; ++cl) {
+            FusedGroup G;
+            G.clog = cl;
+            for (int q = 0; q < count; ++q) {
+                if (clog[q] != cl) continue;
+                int rows, warps;
+                fits(q, cl, rows, warps);
+                const Sizes &z = zs[members[q]];
+                G.count++;
+                G.rows_cap = std::max(G.rows_cap, rows);
+                G.kp_cap = std::max(G.kp_cap, z.kp);
+                G.stride = std::max(G.stride, (z.n + 31) / 32);
+                G.warps = std::max(G.warps, warps);
+            }
+            if (!G.count) continue;
+            const size_t base = fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, 0, 0);
+            if (base > FUSED_SMEM_LIMIT) {
+                if (cl == 3) return HAC_EUNSUPPORTED;
+                for (int q = 0; q < count; ++q) if (clog[q] == cl) clog[q] = cl + 1;
+                again = true;
+                break;
+            }
+            // coordinates of the fallback scan in shared memory when they still fit
+            int nmax = 0;
+            for (int q = 0; q < count; ++q) if (clog[q] == cl) nmax = std::max(nmax, zs[members[q]].n);
+            if (base + (size_t)nmax * 8 <= FUSED_SMEM_LIMIT) G.xy_cap = nmax;
+            // and the lookup lists of this CTA's rows
+            if (fallback_list &&
+                fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, G.xy_cap, G.rows_cap) <=
+                    FUSED_SMEM_LIMIT)
+                G.list_rows = G.rows_cap;
+            groups.push_back(G);
+        }
+        if (!again) break;
+    }
+    order.clear();
+    for (FusedGroup &G : groups) {
+        G.order_off = (int)order.size();
+        std::vector<int32_t> mem;
+        for (int q = 0; q < count; ++q) if (clog[q] == G.clog) mem.push_back(members[q]);
+        std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) {
+            const Sizes &a = zs[x], &c = zs[y];
+            return (long long)a.m * a.n * a.iters > (long long)c.m * c.n * c.iters;
+        });
+        order.insert(order.end(), mem.begin(), mem.end());
+    }
+    return HAC_OK;
+}
+
+// Launches the groups concurrently: group 0 on `s`, the others on their side
+// streams, forked from and joined back into `s`.
+inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order,
+                                 const std::vector<FusedGroup> &groups, int apw, int iters, cudaStream_t s)
+{
+    cudaError_t err = cudaSuccess;
+    for (size_t g = 1; g < groups.size(); ++g) {
+        cudaEventRecord(groups[g].fork, s);
+        cudaStreamWaitEvent(groups[g].side, groups[g].fork, 0);
+    }
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const FusedGroup &G = groups[g];
+        cudaError_t e = launch_fused(d_inst, d_order + G.order_off, G.count, G.clog, apw, G.warps,
+                                     G.rows_cap, G.kp_cap, G.stride, G.xy_cap, G.list_rows, iters,
+                                     g ? G.side : s);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    }
+    for (size_t g = 1; g < groups.size(); ++g) {
+        cudaEventRecord(groups[g].join, groups[g].side);
+        cudaStreamWaitEvent(s, groups[g].join, 0);
+    }
+    return err;
+}
+
+}  // namespace host
+}  // namespace hac
