@@ -216,6 +216,86 @@ int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count
                     const hac_exec *exec, int32_t *const *best_tours, double *best_lens,
                     int32_t *statuses, void *stream);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of decode requests (the paper has no serving layer;
+ * this is how the decoder of Algorithm 1 is offered to a request stream).
+ * A server owns one caller-provided device workspace; each admitted request
+ * takes a region of it (hac_server_request_bytes) that holds its whole state,
+ * pheromone and T_gb included, from admission until its result is polled.
+ * Requests that arrive while others run are admitted whenever a slot and a
+ * region are free, and all admitted requests advance together, each from its
+ * own iteration, in the persistent cluster kernel (hac_exec.fused).  A request
+ * returns the same tour and length as hac_solve on the same instance and
+ * parameters, alone or in any mix.  Inputs are host pointers; the server
+ * copies them during hac_server_submit, so the caller may reuse them at once.
+ * A server is not thread-safe: call it from one host thread at a time.
+ *
+ *   max_slots       requests resident at once (1..4096)
+ *   iters_per_tick  MMAS iterations a tick runs for every running request
+ *   max_n           largest n accepted (3..65534); sizes the pinned staging
+ *   steps_per_tick  0, or a per-tick budget of construction steps per ant: a
+ *                   request of n nodes then runs max(1, min(iters_per_tick,
+ *                   steps_per_tick / n)) iterations a tick, so that small and
+ *                   large requests take about the same time per tick
+ *   exec            ants_per_warp (0 -> 4; 2, 4 or 32), cluster_log2 (the
+ *                   smallest cluster size, log2), fallback_list (0 or 32);
+ *                   fused is implied, the other fields are ignored */
+typedef struct {
+    int32_t max_slots;
+    int32_t iters_per_tick;
+    int32_t max_n;
+    int32_t steps_per_tick;
+    hac_exec exec;
+} hac_server_cfg;
+
+typedef struct hac_server hac_server;
+
+/* Device bytes one request takes from a server's workspace. */
+int hac_server_request_bytes(const hac_instance *in, const hac_params *p, size_t *bytes);
+
+/* Creates a server on `workspace` (device memory, ws_bytes; header of about
+ * max_slots * 1 KB, the rest is the request heap) and `stream`.  Allocates
+ * pinned host staging of about max_slots * (4 * max_n + 512) bytes, one side
+ * stream for preparation and three for concurrent cluster-size groups.
+ * HAC_ENOMEM if the workspace cannot hold the header and a minimal heap. */
+int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_bytes, void *stream,
+                      hac_server **out);
+
+/* Admits a request: checks it (as hac_batch_create does for host inputs),
+ * takes a free slot and the first heap region that fits, uploads the inputs
+ * and enqueues the preparation (Sec. III-A: candidate lists, evidence, kappa,
+ * W; T_NN and the bounds) on the preparation stream.  Returns a ticket > 0.
+ * HAC_EBUSY when no slot or no region is free (retry after polling finished
+ * requests); HAC_EINVAL for n > max_n or a malformed request;
+ * HAC_EUNSUPPORTED when the instance does not fit the cluster kernel. */
+int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *p, uint64_t *ticket);
+
+/* Runs the tick's iterations of every running request (requests
+ * whose preparation has finished join here) and stages the results of the
+ * requests that reach their iteration count.  Asynchronous; keeps at most two
+ * ticks in flight (waits for the tick before the previous one). */
+int hac_server_tick(hac_server *sv);
+
+/* Result of a request: T_gb (n int32, may be NULL) and L_gb (may be NULL).
+ * HAC_EBUSY while the request is still preparing, running or staging;
+ * HAC_EINVAL for an unknown ticket.  On HAC_OK the slot and region are freed
+ * and the ticket is no longer valid.  Does not block. */
+int hac_server_poll(hac_server *sv, uint64_t ticket, int32_t *tour, double *len);
+
+/* Requests resident (admitted, not yet polled), finished requests waiting to
+ * be polled, and free heap bytes.  With device_error non-NULL the call also
+ * synchronises and reports the first device-side error of the preparation
+ * kernels (0 if none).  Any pointer may be NULL. */
+int hac_server_stats(hac_server *sv, int32_t *resident, int32_t *finished, size_t *free_bytes,
+                     int32_t *device_error);
+
+/* Kernel launches issued so far (preparation and cluster kernels). */
+int hac_server_launches(hac_server *sv, int64_t *launches);
+
+/* Synchronises the server's streams and releases its host resources; the
+ * workspace may be reused afterwards.  Unpolled results are dropped. */
+int hac_server_destroy(hac_server *sv);
+
 /* ------------------------------------------------------------------ no allocation
  * Decode one instance without any device allocation, for callers that cannot
  * call cudaMalloc: a host application whose allocator or memory budget owns

@@ -297,7 +297,7 @@ static int enqueue_fused(hac_batch *bt, int iters)
 {
     cudaError_t err = cudaSuccess;
     const int k = timed(bt, 3, [&] {
-        err = launch_groups(bt->d_inst, bt->d_order, bt->groups, bt->ex.ants_per_warp, iters, bt->stream);
+        err = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups, bt->ex.ants_per_warp, iters, bt->stream);
         return (int)bt->groups.size();
     });
     if (err != cudaSuccess) { g_last_cuda = (int)err; return HAC_ECUDA; }

@@ -28,6 +28,7 @@ namespace hac {
 struct FusedArgs {
     const DevInst *insts;
     const int32_t *order;     // cluster -> instance
+    const int32_t *iters_of;  // cluster -> iterations to run (null: iters_request for all)
     int iters_request;
     int rows_cap;             // shared-memory rows per CTA (max over the group)
     int kp_cap;               // max k_pad of the group
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
     const int t0 = st->t;
     cl.sync();
 
-    const int t_end = min(I.iters, t0 + A.iters_request);
+    const int t_end = min(I.iters, t0 + (A.iters_of ? A.iters_of[cid] : A.iters_request));
     const int apc = (m + C - 1) >> CLOG;   // ants per CTA
     const int a_lo = rank * apc, a_hi = min(m, a_lo + apc);
     const float omega = __double2float_rn(__dsub_rn(1.0, I.rho));
@@ -188,11 +189,11 @@ size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride
            (size_t)list_rows * FBL * 2;
 }
 
-cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, int clusters, int clog,
-                         int apw, int warps, int rows_cap, int kp_cap, int stride, int xy_cap,
-                         int list_rows, int iters, cudaStream_t s)
+cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
+                         int clusters, int clog, int apw, int warps, int rows_cap, int kp_cap, int stride,
+                         int xy_cap, int list_rows, int iters, cudaStream_t s)
 {
-    FusedArgs A{d_inst, d_order, iters, rows_cap, kp_cap, stride, warps, apw, xy_cap, list_rows};
+    FusedArgs A{d_inst, d_order, d_iters, iters, rows_cap, kp_cap, stride, warps, apw, xy_cap, list_rows};
     const size_t smem = fused_smem_bytes(rows_cap, kp_cap, warps, apw, stride, xy_cap, list_rows);
 #define CLUSTER_SWITCH(APWV, NGV) \
     switch (clog) { \

@@ -240,12 +240,14 @@ int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_l
                      int warps_per_block, int max_n, int max_kp, int count, cudaStream_t s);
 int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
                           int slotmap_len, bool any_ls, cudaStream_t s);
-// fused cluster kernel (fused.cu): one cluster of 2^clog CTAs per instance
+// fused cluster kernel (fused.cu): one cluster of 2^clog CTAs per instance;
+// d_iters (parallel to d_order, may be null) gives each cluster its own
+// iteration count instead of `iters`
 size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride, int xy_cap,
                         int list_rows);
-cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, int clusters, int clog,
-                         int apw, int warps, int rows_cap, int kp_cap, int stride, int xy_cap,
-                         int list_rows, int iters, cudaStream_t s);
+cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
+                         int clusters, int clog, int apw, int warps, int rows_cap, int kp_cap, int stride,
+                         int xy_cap, int list_rows, int iters, cudaStream_t s);
 constexpr size_t FUSED_SMEM_LIMIT = 220 * 1024;   // dynamic shared memory per CTA we allow
 
 }  // namespace hac

@@ -377,8 +377,9 @@ inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &mem
 }
 
 // Launches the groups concurrently: group 0 on `s`, the others on their side
-// streams, forked from and joined back into `s`.
-inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order,
+// streams, forked from and joined back into `s`.  d_iters (parallel to
+// d_order, may be null) holds per-instance iteration counts.
+inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
                                  const std::vector<FusedGroup> &groups, int apw, int iters, cudaStream_t s)
 {
     cudaError_t err = cudaSuccess;
@@ -388,7 +389,8 @@ inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order,
     }
     for (size_t g = 0; g < groups.size(); ++g) {
         const FusedGroup &G = groups[g];
-        cudaError_t e = launch_fused(d_inst, d_order + G.order_off, G.count, G.clog, apw, G.warps,
+        cudaError_t e = launch_fused(d_inst, d_order + G.order_off, d_iters ? d_iters + G.order_off : nullptr,
+                                     G.count, G.clog, apw, G.warps,
                                      G.rows_cap, G.kp_cap, G.stride, G.xy_cap, G.list_rows, iters,
                                      g ? G.side : s);
         if (e != cudaSuccess && err == cudaSuccess) err = e;

@@ -54,6 +54,11 @@ class hac_exec(C.Structure):
                 ("profile", C.c_int32), ("cluster_log2", C.c_int32)]
 
 
+class hac_server_cfg(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("iters_per_tick", C.c_int32), ("max_n", C.c_int32),
+                ("steps_per_tick", C.c_int32), ("exec", hac_exec)]
+
+
 _LIB = None
 
 # every symbol include/heataco.h declares, with (restype, argtypes)
@@ -85,6 +90,18 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "hac_solve_noalloc": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32,
                                     C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "hac_server_request_bytes": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params),
+                                           C.POINTER(C.c_size_t)]),
+    "hac_server_create": (C.c_int, [C.POINTER(hac_server_cfg), C.c_void_p, C.c_size_t, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
+    "hac_server_submit": (C.c_int, [C.c_void_p, C.POINTER(hac_instance), C.POINTER(hac_params),
+                                    C.POINTER(C.c_uint64)]),
+    "hac_server_tick": (C.c_int, [C.c_void_p]),
+    "hac_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_double)]),
+    "hac_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_size_t), C.POINTER(C.c_int32)]),
+    "hac_server_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "hac_server_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -309,3 +326,91 @@ def solve_batch(instances, params, exec_=None, inputs_on_device=False):
 def solve(instance, params, exec_=None):
     tours, lens = solve_batch([instance], [params], exec_)
     return tours[0], float(lens[0])
+
+
+# ------------------------------------------------------------------ serving
+
+def hac_server_request_bytes(instance, params) -> int:
+    m = _Marshal([instance], [params], False)
+    out = C.c_size_t(0)
+    _check(_lib().hac_server_request_bytes(m.ins, m.ps, C.byref(out)), "hac_server_request_bytes")
+    return out.value
+
+
+class Server:
+    """Continuous-batching decode server (hac_server_* calls) on a device workspace
+    of `ws_bytes` bytes (a uint8 torch tensor)."""
+
+    def __init__(self, ws_bytes: int, max_slots: int = 64, iters_per_tick: int = 10, max_n: int = 10000,
+                 exec_=None, stream=None, workspace=None, steps_per_tick: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise HeatACOError(HAC_ECUDA, "no CUDA device")
+        if workspace is None or workspace.numel() < ws_bytes:
+            workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.cfg = hac_server_cfg(max_slots, iters_per_tick, max_n, steps_per_tick,
+                                  exec_ if exec_ is not None else make_exec(fused=1))
+        self.sizes = {}
+        h = C.c_void_p()
+        _check(_lib().hac_server_create(C.byref(self.cfg), C.c_void_p(workspace.data_ptr()),
+                                        C.c_size_t(workspace.numel()), C.c_void_p(self.stream.cuda_stream),
+                                        C.byref(h)), "hac_server_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib().hac_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, instance, params):
+        """Ticket (int > 0), or None when no slot or memory is free (HAC_EBUSY)."""
+        m = _Marshal([instance], [params], False)
+        t = C.c_uint64(0)
+        st = _lib().hac_server_submit(self.h, m.ins, m.ps, C.byref(t))
+        if st == HAC_EBUSY:
+            return None
+        _check(st, "hac_server_submit")
+        self.sizes[t.value] = instance.n
+        return t.value
+
+    def tick(self):
+        _check(_lib().hac_server_tick(self.h), "hac_server_tick")
+
+    def poll(self, ticket: int):
+        """(tour, length) once finished, else None."""
+        tour = np.empty(self.sizes[ticket], np.int32)
+        ln = C.c_double(0)
+        st = _lib().hac_server_poll(self.h, ticket, tour.ctypes.data, C.byref(ln))
+        if st == HAC_EBUSY:
+            return None
+        _check(st, "hac_server_poll")
+        del self.sizes[ticket]
+        return tour, ln.value
+
+    def stats(self, device_error: bool = False) -> dict:
+        r, f, fb, de = C.c_int32(0), C.c_int32(0), C.c_size_t(0), C.c_int32(0)
+        _check(_lib().hac_server_stats(self.h, C.byref(r), C.byref(f), C.byref(fb),
+                                       C.byref(de) if device_error else None), "hac_server_stats")
+        out = dict(resident=r.value, finished=f.value, free_bytes=fb.value)
+        if device_error:
+            out["device_error"] = de.value
+        return out
+
+    def launches(self) -> int:
+        v = C.c_int64(0)
+        _check(_lib().hac_server_launches(self.h, C.byref(v)), "hac_server_launches")
+        return v.value

@@ -94,3 +94,31 @@ def test_host_data_validation_before_cuda(lib):
     assert lib.hac_batch_create(m.ins, m.ps, 1, 0, None, ws, None, None, C.byref(h)) == heataco.HAC_ENOMEM
     assert lib.hac_batch_create(m.ins, m.ps, 1, 0, dummy, C.c_size_t(ws.value - 1024), None, None,
                                 C.byref(h)) == heataco.HAC_ENOMEM
+
+
+def test_server_host_checks_before_cuda(lib):
+    from paper_2601_19041_gb300 import heataco
+    pts = np.random.default_rng(1).random((60, 2)).astype(np.float32)
+    inst = euclid(pts)
+    small, big = params(m=8, k=8, iterations=3, rho=0.2), params(m=64, k=20, iterations=300, rho=0.2)
+    rs, rb = heataco.hac_server_request_bytes(inst, small), heataco.hac_server_request_bytes(inst, big)
+    assert 0 < rs < rb and rs % 256 == 0 and rb % 256 == 0
+    assert rb >= heataco.hac_batch_workspace_size([inst], [big]) - 4096
+    h = C.c_void_p()
+    dummy = C.c_void_p(256)          # never dereferenced: the checks fail first
+    for cfg in (heataco.hac_server_cfg(0, 1, 100, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 0, 100, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 2, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 70000, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 100, 0, heataco.make_exec(ants_per_warp=1)),
+                heataco.hac_server_cfg(4, 1, 100, 0, heataco.make_exec(fallback_list=7)),
+                heataco.hac_server_cfg(4, 1, 100, -1, heataco.make_exec())):
+        assert lib.hac_server_create(C.byref(cfg), dummy, C.c_size_t(1 << 30), None, C.byref(h)) == \
+            heataco.HAC_EINVAL
+        assert not h.value
+    cfg = heataco.hac_server_cfg(4, 1, 100, 0, heataco.make_exec())
+    assert lib.hac_server_create(C.byref(cfg), dummy, C.c_size_t(4096), None, C.byref(h)) == heataco.HAC_ENOMEM
+    assert lib.hac_server_create(None, dummy, C.c_size_t(1 << 30), None, C.byref(h)) == heataco.HAC_EINVAL
+    for call in (lambda: lib.hac_server_tick(None), lambda: lib.hac_server_destroy(None),
+                 lambda: lib.hac_server_poll(None, 1, None, None)):
+        assert call() == heataco.HAC_EINVAL
