@@ -104,7 +104,9 @@ typedef struct {
 typedef struct {
     int32_t ants_per_warp;    /* 1, 2 or 4 ants share one warp (8-lane segments); 0 = auto */
     int32_t warps_per_block;  /* construction block size in warps; 0 = auto */
-    int32_t use_graph;        /* 1: capture the iteration loop in a CUDA graph */
+    int32_t use_graph;        /* 1: capture the iteration loop (per-step kernels: 10 iterations
+                                 per graph; fused: the concurrent group launches) in a CUDA
+                                 graph, replayed; needs a non-NULL stream */
     int32_t fused;            /* 1: persistent fused construct+update kernel; 0: per-step launches */
     int32_t fallback_list;    /* 32: look up the 32 nearest nodes (key order) before scanning; 0: scan only */
     int32_t profile;          /* 1: bracket every kernel group with CUDA events (no graphs) */
@@ -198,6 +200,22 @@ int hac_batch_launches(hac_batch *bt, int64_t *launches);
  *   global best, pheromone update), 2 preparation, 3 fused iterations
  *   (construction and tail in the persistent cluster kernel).  Synchronises. */
 int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *launches);
+
+/* Autotuner: decodes the batch's first trial_iters + 1 iterations once per
+ * candidate execution layout and returns in *best the layout whose last
+ * trial_iters iterations took the least device time (CUDA events on
+ * `stream`), with use_graph = 1, and that time per iteration in *ms_per_iter
+ * (may be NULL).  Candidates: the fused cluster kernel with 2, 4 or 32 ants
+ * per warp, smallest cluster 1, 2 or 4 CTAs, with and without the 32-entry
+ * nearest-unvisited lookup list; the per-step kernels with 1, 2 or 4 ants per
+ * warp and 4 or 8 warps per block.  No layout changes a result, so the choice
+ * is a matter of speed only; the method's parameters (m, k, ...) are never
+ * changed.  Uses `workspace` (hac_batch_workspace_size bytes) for each trial
+ * in turn; synchronises `stream`.  Candidates an instance does not support
+ * are skipped. */
+int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t count,
+                       int32_t inputs_on_device, void *workspace, size_t ws_bytes, int32_t trial_iters,
+                       void *stream, hac_exec *best, double *ms_per_iter);
 
 /* Releases the host handle; the workspace can be reused afterwards.  Does not
  * synchronise: the caller must not reuse the workspace before the stream has

@@ -40,6 +40,8 @@ struct hac_batch {
     std::vector<int> t_host;
     cudaGraphExec_t gexec = nullptr;
     int graph_kernels = 0;          // kernels inside one graph replay
+    cudaGraphExec_t fexec = nullptr;   // fused groups (fork/join included) for fexec_iters iterations
+    int fexec_iters = -1;
     long long launches = 0;         // kernels issued so far
     // profiling: event pairs per kernel group, folded into totals on read
     std::vector<cudaEvent_t> ev_pool;
@@ -295,6 +297,25 @@ static int enqueue_iteration(hac_batch *bt)
 // fork/join region of a given iteration count is captured once and replayed
 static int enqueue_fused(hac_batch *bt, int iters)
 {
+    if (bt->ex.use_graph && !bt->ex.profile && bt->stream != nullptr) {
+        if (!bt->fexec || bt->fexec_iters != iters) {
+            if (bt->fexec) { cudaGraphExecDestroy(bt->fexec); bt->fexec = nullptr; }
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e1 = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups, bt->ex.ants_per_warp,
+                                           iters, bt->stream);
+            cudaError_t e2 = cudaStreamEndCapture(bt->stream, &g);
+            if (e1 != cudaSuccess) { g_last_cuda = (int)e1; if (e2 == cudaSuccess) cudaGraphDestroy(g); return HAC_ECUDA; }
+            CK(e2);
+            cudaError_t e3 = cudaGraphInstantiate(&bt->fexec, g, 0);
+            cudaGraphDestroy(g);
+            CK(e3);
+            bt->fexec_iters = iters;
+        }
+        CK(cudaGraphLaunch(bt->fexec, bt->stream));
+        bt->launches += (long long)bt->groups.size();
+        return HAC_OK;
+    }
     cudaError_t err = cudaSuccess;
     const int k = timed(bt, 3, [&] {
         err = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups, bt->ex.ants_per_warp, iters, bt->stream);
@@ -478,6 +499,7 @@ int hac_batch_destroy(hac_batch *bt)
 {
     if (!bt) return HAC_EINVAL;
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->fexec) cudaGraphExecDestroy(bt->fexec);
     for (cudaEvent_t e : bt->ev_pool) cudaEventDestroy(e);
     for (FusedGroup &G : bt->groups) {
         if (G.side) cudaStreamDestroy(G.side);
@@ -501,6 +523,72 @@ int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count
     if (statuses)
         for (int b = 0; b < count; ++b) statuses[b] = st;
     return st;
+}
+
+int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t count,
+                       int32_t inputs_on_device, void *workspace, size_t ws_bytes, int32_t trial_iters,
+                       void *stream, hac_exec *best, double *ms_per_iter)
+{
+    if (!best || trial_iters < 1) return HAC_EINVAL;
+    Plan P;
+    int st = plan_batch(ins, ps, count, inputs_on_device, P);
+    if (st) return st;
+    if (!workspace || ws_bytes < P.total) return HAC_ENOMEM;
+    // candidates: every execution layout (none changes a result)
+    std::vector<hac_exec> cands;
+    for (int apw : {4, 2, 32})
+        for (int clog = 0; clog <= 2; ++clog)
+            for (int fbl : {FBL_LEN, 0}) {
+                hac_exec e;
+                hac_exec_default(&e);
+                e.fused = 1; e.ants_per_warp = apw; e.cluster_log2 = clog; e.fallback_list = fbl;
+                cands.push_back(e);
+            }
+    for (int apw : {4, 2, 1})
+        for (int wpb : {4, 8}) {
+            hac_exec e;
+            hac_exec_default(&e);
+            e.fused = 0; e.ants_per_warp = apw; e.warps_per_block = wpb; e.fallback_list = FBL_LEN;
+            cands.push_back(e);
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) { cudaEventDestroy(ev[0]); return HAC_ECUDA; }
+    double best_ms = -1.0;
+    int rc = HAC_OK;
+    for (const hac_exec &c : cands) {
+        hac_exec e = c;
+        e.use_graph = 0;
+        hac_batch *bt = nullptr;
+        st = hac_batch_create(ins, ps, count, inputs_on_device, workspace, ws_bytes, &e, stream, &bt);
+        if (st == HAC_EUNSUPPORTED) continue;
+        if (st) { rc = st; break; }
+        if (e.fused && !bt->ex.fused) {   // does not fit the cluster kernel: same as a per-step candidate
+            hac_batch_destroy(bt);
+            continue;
+        }
+        float ms = 0.f;
+        st = hac_batch_iterate(bt, 1);
+        if (!st && cudaEventRecord(ev[0], s) != cudaSuccess) st = HAC_ECUDA;
+        if (!st) st = hac_batch_iterate(bt, trial_iters);
+        if (!st && cudaEventRecord(ev[1], s) != cudaSuccess) st = HAC_ECUDA;
+        if (!st) st = hac_batch_sync(bt);
+        if (!st && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) st = HAC_ECUDA;
+        hac_batch_destroy(bt);
+        if (st) { rc = st; break; }
+        if (best_ms < 0.0 || ms < best_ms) {
+            best_ms = ms;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    if (best_ms < 0.0) return HAC_EUNSUPPORTED;
+    best->use_graph = 1;
+    if (ms_per_iter) *ms_per_iter = best_ms / trial_iters;
+    return HAC_OK;
 }
 
 int hac_solve(const hac_instance *in, const hac_params *p, int32_t inputs_on_device,

@@ -90,6 +90,9 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "hac_solve_noalloc": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32,
                                     C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    "hac_batch_autotune": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_int32,
+                                     C.c_void_p, C.c_size_t, C.c_int32, C.c_void_p, C.POINTER(hac_exec),
+                                     C.POINTER(C.c_double)]),
     "hac_server_request_bytes": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params),
                                            C.POINTER(C.c_size_t)]),
     "hac_server_create": (C.c_int, [C.POINTER(hac_server_cfg), C.c_void_p, C.c_size_t, C.c_void_p,
@@ -317,6 +320,24 @@ class Batch:
         return ms.value, k.value
 
 
+def autotune(instances, params, trial_iters=10, inputs_on_device=False, stream=None, workspace=None):
+    """(best hac_exec, ms per iteration) from hac_batch_autotune."""
+    import torch
+    m = _Marshal(instances, params, inputs_on_device)
+    size = C.c_size_t(0)
+    _check(_lib().hac_batch_workspace_size(m.ins, m.ps, len(instances), int(inputs_on_device), C.byref(size)),
+           "hac_batch_workspace_size")
+    if workspace is None or workspace.numel() < size.value:
+        workspace = torch.empty(size.value, dtype=torch.uint8, device="cuda")
+    stream = stream if stream is not None else torch.cuda.Stream()
+    best, ms = hac_exec(), C.c_double(0)
+    _check(_lib().hac_batch_autotune(m.ins, m.ps, len(instances), int(inputs_on_device),
+                                     C.c_void_p(workspace.data_ptr()), C.c_size_t(workspace.numel()),
+                                     trial_iters, C.c_void_p(stream.cuda_stream), C.byref(best), C.byref(ms)),
+           "hac_batch_autotune")
+    return best, ms.value
+
+
 def solve_batch(instances, params, exec_=None, inputs_on_device=False):
     with Batch(instances, params, exec_, inputs_on_device) as bt:
         bt.run()
@@ -392,9 +413,10 @@ class Server:
 
     def poll(self, ticket: int):
         """(tour, length) once finished, else None."""
-        tour = np.empty(self.sizes[ticket], np.int32)
+        n = self.sizes.get(ticket)
+        tour = np.empty(n if n is not None else 0, np.int32)
         ln = C.c_double(0)
-        st = _lib().hac_server_poll(self.h, ticket, tour.ctypes.data, C.byref(ln))
+        st = _lib().hac_server_poll(self.h, ticket, tour.ctypes.data if n is not None else None, C.byref(ln))
         if st == HAC_EBUSY:
             return None
         _check(st, "hac_server_poll")
