@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--steps-per-tick", type=int, default=4000, help="serve: construction steps per ant per tick")
     ap.add_argument("--iters-per-tick", type=int, default=10, help="serve: iteration cap per tick")
     ap.add_argument("--slots", type=int, default=512, help="serve: resident request slots")
+    ap.add_argument("--step-min-n", type=int, default=3000,
+                    help="serve: requests with n >= this run on the per-step kernels (0: cluster kernel only)")
+    ap.add_argument("--step-apw", type=int, default=1, help="serve: ants per warp of the per-step route")
     return ap.parse_args()
 
 
@@ -505,7 +508,8 @@ def run_serve(args):
     need = sum(heataco.hac_server_request_bytes(q.inst, q.params) for q in reqs)
     ws_bytes = int(min(need + (256 << 20), 0.6 * free))      # admission follows this budget
     srv = heataco.Server(ws_bytes, max_slots=args.slots, iters_per_tick=args.iters_per_tick,
-                         max_n=10000, steps_per_tick=args.steps_per_tick,
+                         max_n=10000, steps_per_tick=args.steps_per_tick, step_min_n=args.step_min_n,
+                         step_ants_per_warp=args.step_apw, step_warps_per_block=8,
                          exec_=heataco.make_exec(ants_per_warp=args.apw or 4, fused=1, fallback_list=args.fbl,
                                                  cluster_log2=args.clog))
     # warm-up: a few small requests through the same server (kernel loading, clocks)
@@ -601,6 +605,7 @@ def run_serve(args):
                    "arrival_span_s": reqs[-1].arrival - reqs[0].arrival,
                    "workspace_bytes": ws_bytes, "slots": args.slots,
                    "steps_per_tick": args.steps_per_tick, "iters_per_tick": args.iters_per_tick,
+                   "step_min_n": args.step_min_n, "step_ants_per_warp": args.step_apw,
                    "l2": "resident request state of several GB (> 129 MB L2)",
                    "inputs": "host numpy arrays, copied at admission; results read back at poll"},
         "latency_ms": {"p50": pct(lat, 50), "p90": pct(lat, 90), "p99": pct(lat, 99),

@@ -255,6 +255,14 @@ int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count
  *                   request of n nodes then runs max(1, min(iters_per_tick,
  *                   steps_per_tick / n)) iterations a tick, so that small and
  *                   large requests take about the same time per tick
+ *   step_min_n      0, or the n from which requests run on the per-step
+ *                   kernels (rows through L2, ants of many instances on each
+ *                   SM) instead of the cluster kernel (candidate table in
+ *                   the shared memory of 2^c SMs, which leaves few ants per
+ *                   SM for large n); those requests all run the smallest
+ *                   budget among them each tick
+ *   step_ants_per_warp, step_warps_per_block
+ *                   layout of that route (0 -> 1 and 8; 1, 2 or 4 and 1..8)
  *   exec            ants_per_warp (0 -> 4; 2, 4 or 32), cluster_log2 (the
  *                   smallest cluster size, log2), fallback_list (0 or 32);
  *                   fused is implied, the other fields are ignored */
@@ -263,6 +271,9 @@ typedef struct {
     int32_t iters_per_tick;
     int32_t max_n;
     int32_t steps_per_tick;
+    int32_t step_min_n;
+    int32_t step_ants_per_warp;
+    int32_t step_warps_per_block;
     hac_exec exec;
 } hac_server_cfg;
 
@@ -273,8 +284,10 @@ int hac_server_request_bytes(const hac_instance *in, const hac_params *p, size_t
 
 /* Creates a server on `workspace` (device memory, ws_bytes; header of about
  * max_slots * 1 KB, the rest is the request heap) and `stream`.  Allocates
- * pinned host staging of about max_slots * (4 * max_n + 512) bytes, one side
- * stream for preparation and three for concurrent cluster-size groups.
+ * pinned host staging of about max_slots * (4 * max_n + 512) bytes (and,
+ * with step_min_n > 0, per-tick work tables of about max_slots * (16 KB +
+ * max_n / 4) bytes, twice, on both sides), one side stream for preparation,
+ * three for concurrent cluster-size groups and one for the per-step route.
  * HAC_ENOMEM if the workspace cannot hold the header and a minimal heap. */
 int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_bytes, void *stream,
                       hac_server **out);
@@ -285,7 +298,8 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
  * W; T_NN and the bounds) on the preparation stream.  Returns a ticket > 0.
  * HAC_EBUSY when no slot or no region is free (retry after polling finished
  * requests); HAC_EINVAL for n > max_n or a malformed request;
- * HAC_EUNSUPPORTED when the instance does not fit the cluster kernel. */
+ * HAC_EUNSUPPORTED when a request routed to the cluster kernel does not fit
+ * it. */
 int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *p, uint64_t *ticket);
 
 /* Runs the tick's iterations of every running request (requests

@@ -12,13 +12,17 @@
 //           memory), uploads the inputs and runs the preparation kernels
 //           (candidate lists, evidence, kappa, W, T_NN, bounds, tau_0) on a
 //           side stream, so that preparation overlaps the running iterations.
-//   tick:   admits the requests whose preparation has finished, then runs up
-//           to iters_per_tick MMAS iterations of every admitted request in
-//           one launch of the persistent cluster kernel per cluster size
-//           (the batch API's fused path).  Each instance continues from its
-//           own iteration counter, so requests at different points of their
-//           search share a launch.  Requests that reach their iteration count
-//           get their T_gb and L_gb copied to pinned host staging.
+//   tick:   admits the requests whose preparation has finished, then runs
+//           the tick's MMAS iterations of every admitted request.  Requests
+//           below step_min_n nodes run in one launch of the persistent
+//           cluster kernel per cluster size (the batch API's fused path);
+//           larger ones, whose candidate tables would pin several SMs for a
+//           few ants, run the per-step kernels (rows read through L2, many
+//           instances per SM) on a stream of their own, concurrently.  Each
+//           instance continues from its own iteration counter, so requests
+//           at different points of their search share a launch.  Requests
+//           that reach their iteration count get their T_gb and L_gb copied
+//           to pinned host staging.
 //   poll:   returns a finished request's result and frees its slot and region.
 //
 // Per request the arithmetic is exactly that of hac_solve (the random numbers
@@ -43,6 +47,7 @@ struct Slot {
     uint64_t ticket = 0;
     size_t off = 0, bytes = 0;      // heap region (offset from the heap base)
     Sizes z{};
+    int route = 0;                  // 0: cluster kernel, 1: per-step kernels
     int t = 0;                      // iterations enqueued so far
     cudaEvent_t ready = nullptr;    // preparation done (prep stream)
     cudaEvent_t done = nullptr;     // result staged (main stream)
@@ -97,6 +102,14 @@ struct hac_server {
     cudaStream_t side[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t fork[3] = {nullptr, nullptr, nullptr}, join[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t tick_ev[2] = {nullptr, nullptr};
+    // per-step route: stream, fork/join, per-tick compact instance and work tables
+    cudaStream_t sstream = nullptr;
+    cudaEvent_t sfork = nullptr, sjoin = nullptr;
+    hac_exec sex{};
+    size_t swarp_cap = 0, sslot_cap = 0;
+    DevInst *d_sinst[2] = {nullptr, nullptr}, *h_sinst[2] = {nullptr, nullptr};
+    int4 *d_swarp[2] = {nullptr, nullptr}, *h_swarp[2] = {nullptr, nullptr};
+    int2 *d_sslot[2] = {nullptr, nullptr}, *h_sslot[2] = {nullptr, nullptr};
     bool tick_rec[2] = {false, false};
     long long ticks = 0;
     long long launches = 0;
@@ -151,12 +164,29 @@ int fits_fused(const hac_server *sv, const Sizes &z)
     return plan_groups(one, mem, sv->ex.ants_per_warp, sv->ex.cluster_log2, sv->ex.fallback_list, g, o);
 }
 
-size_t header_bytes(const hac_server_cfg &c)
+// per-tick tables of the per-step route: warp and slot work items
+void step_caps(const hac_server_cfg &c, int apw, size_t &warps, size_t &slots)
+{
+    warps = slots = 0;
+    if (c.step_min_n <= 0) return;
+    warps = (size_t)c.max_slots * ((HAC_MMAX + apw - 1) / apw);
+    slots = (size_t)c.max_slots * (((size_t)c.max_n * HAC_KMAX + SLOTS_PER_BLOCK - 1) / SLOTS_PER_BLOCK);
+}
+
+size_t header_bytes(const hac_server_cfg &c, int step_apw)
 {
     Arena A;
     A.take((size_t)c.max_slots * sizeof(DevInst));
     for (int q = 0; q < 4; ++q) A.take((size_t)c.max_slots * sizeof(int32_t));
     A.take(sizeof(int));
+    size_t w, s;
+    step_caps(c, step_apw, w, s);
+    if (c.step_min_n > 0)
+        for (int q = 0; q < 2; ++q) {
+            A.take((size_t)c.max_slots * sizeof(DevInst));
+            A.take(w * sizeof(int4));
+            A.take(s * sizeof(int2));
+        }
     return (A.off + 255) & ~(size_t)255;
 }
 
@@ -182,6 +212,47 @@ int enqueue_groups(hac_server *sv, std::vector<FusedGroup> &groups, const int32_
     return HAC_OK;
 }
 
+// The per-step route of one tick: a compact DevInst array of the members (its
+// entries point into the members' resident regions), their warp and slot work
+// tables, and min over members of the tick's iteration budget, each iteration
+// one construction launch and one iteration tail, on the route's own stream.
+int enqueue_step_route(hac_server *sv, const std::vector<int> &mem, int par)
+{
+    const int apw = sv->sex.ants_per_warp;
+    DevInst *hI = sv->h_sinst[par];
+    int4 *hw = sv->h_swarp[par];
+    int2 *hs = sv->h_sslot[par];
+    size_t nw = 0, ns = 0;
+    int it = sv->cfg.iters_per_tick, max_n = 0, max_kp = 0;
+    bool any_ls = false;
+    for (size_t b = 0; b < mem.size(); ++b) {
+        const Slot &S = sv->slots[mem[b]];
+        hI[b] = sv->hi[mem[b]];
+        for (int a = 0; a < S.z.m; a += apw) hw[nw++] = make_int4((int)b, a, 0, 0);
+        const size_t SS = (size_t)S.z.n * S.z.kp;
+        for (size_t q = 0; q < SS; q += SLOTS_PER_BLOCK) hs[ns++] = make_int2((int)b, (int)q);
+        it = std::min(it, tick_iters(sv, S));
+        max_n = std::max(max_n, S.z.n);
+        max_kp = std::max(max_kp, S.z.kp);
+        any_ls |= S.z.ls != 0;
+    }
+    const int count = (int)mem.size();
+    cudaStream_t ss = sv->sstream;
+    CK(cudaEventRecord(sv->sfork, sv->stream));
+    CK(cudaStreamWaitEvent(ss, sv->sfork, 0));
+    CK(cudaMemcpyAsync(sv->d_sinst[par], hI, count * sizeof(DevInst), cudaMemcpyHostToDevice, ss));
+    CK(cudaMemcpyAsync(sv->d_swarp[par], hw, nw * sizeof(int4), cudaMemcpyHostToDevice, ss));
+    CK(cudaMemcpyAsync(sv->d_sslot[par], hs, ns * sizeof(int2), cudaMemcpyHostToDevice, ss));
+    for (int q = 0; q < it; ++q) {
+        sv->launches += launch_construct(sv->d_sinst[par], sv->d_swarp[par], (int)nw, apw,
+                                         sv->sex.warps_per_block, max_n, max_kp, count, ss);
+        sv->launches += launch_iteration_tail(sv->d_sinst[par], count, sv->d_sslot[par], (int)ns, any_ls, ss);
+    }
+    CK(cudaGetLastError());
+    for (int q : mem) sv->slots[q].t += it;
+    return HAC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -203,8 +274,11 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
     *out = nullptr;
     const hac_server_cfg c = *cfg;
     if (c.max_slots < 1 || c.max_slots > 4096 || c.iters_per_tick < 1 || c.max_n < 3 || c.max_n > 65534 ||
-        c.steps_per_tick < 0)
+        c.steps_per_tick < 0 || c.step_min_n < 0)
         return HAC_EINVAL;
+    const int s_apw = c.step_ants_per_warp ? c.step_ants_per_warp : 1;
+    const int s_wpb = c.step_warps_per_block ? c.step_warps_per_block : 8;
+    if ((s_apw != 1 && s_apw != 2 && s_apw != 4) || s_wpb < 1 || s_wpb > 8) return HAC_EINVAL;
     hac_exec ex = c.exec;
     if (ex.ants_per_warp == 0) ex.ants_per_warp = 4;
     if (ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 32) return HAC_EINVAL;
@@ -212,7 +286,7 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
     if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
     ex.fused = 1;
     ex.profile = 0;
-    const size_t hdr = header_bytes(c);
+    const size_t hdr = header_bytes(c, s_apw);
     if (!workspace || ws_bytes < hdr + 256 + 4096) return HAC_ENOMEM;
 
     hac_server *sv = new (std::nothrow) hac_server;
@@ -228,6 +302,17 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
     sv->d_iters[0] = (int32_t *)(B + A.take((size_t)c.max_slots * sizeof(int32_t)));
     sv->d_iters[1] = (int32_t *)(B + A.take((size_t)c.max_slots * sizeof(int32_t)));
     sv->d_err = (int *)(B + A.take(sizeof(int)));
+    sv->sex = ex;
+    sv->sex.fused = 0;
+    sv->sex.ants_per_warp = s_apw;
+    sv->sex.warps_per_block = s_wpb;
+    step_caps(c, s_apw, sv->swarp_cap, sv->sslot_cap);
+    if (c.step_min_n > 0)
+        for (int q = 0; q < 2; ++q) {
+            sv->d_sinst[q] = (DevInst *)(B + A.take((size_t)c.max_slots * sizeof(DevInst)));
+            sv->d_swarp[q] = (int4 *)(B + A.take(sv->swarp_cap * sizeof(int4)));
+            sv->d_sslot[q] = (int2 *)(B + A.take(sv->sslot_cap * sizeof(int2)));
+        }
     sv->heap = B + hdr;
     sv->heap_bytes = ((uintptr_t)workspace + ws_bytes - (uintptr_t)sv->heap) & ~(size_t)255;
     sv->free_list.push_back(Block{0, sv->heap_bytes});
@@ -248,6 +333,21 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
         return fail(e);
     sv->h_order[0] = (int32_t *)(sv->pinned + stage * c.max_slots);
     sv->h_order[1] = (int32_t *)(sv->pinned + stage * c.max_slots + ord);
+    if (c.step_min_n > 0) {
+        const size_t per = (size_t)c.max_slots * sizeof(DevInst) + sv->swarp_cap * sizeof(int4) +
+                           sv->sslot_cap * sizeof(int2);
+        char *hp = nullptr;
+        if ((e = cudaHostAlloc((void **)&hp, 2 * per, cudaHostAllocDefault)) != cudaSuccess) return fail(e);
+        for (int q = 0; q < 2; ++q) {   // the block is released through h_sinst[0]
+            char *b = hp + q * per;
+            sv->h_sinst[q] = (DevInst *)b;
+            sv->h_swarp[q] = (int4 *)(b + (size_t)c.max_slots * sizeof(DevInst));
+            sv->h_sslot[q] = (int2 *)(b + (size_t)c.max_slots * sizeof(DevInst) + sv->swarp_cap * sizeof(int4));
+        }
+        if ((e = cudaStreamCreateWithFlags(&sv->sstream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+        if ((e = cudaEventCreateWithFlags(&sv->sfork, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+        if ((e = cudaEventCreateWithFlags(&sv->sjoin, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+    }
     for (int q = 0; q < c.max_slots; ++q) {
         Slot &S = sv->slots[q];
         S.h_tour = (int32_t *)(sv->pinned + stage * q);
@@ -277,7 +377,8 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     if (st) return st;
     if (z.n > sv->cfg.max_n) return HAC_EINVAL;
     if ((st = check_host_data(*in))) return st;
-    if ((st = fits_fused(sv, z))) return st;
+    const int route = sv->cfg.step_min_n > 0 && z.n >= sv->cfg.step_min_n ? 1 : 0;
+    if (!route && (st = fits_fused(sv, z))) return st;
     int q = 0;
     while (q < sv->cfg.max_slots && sv->slots[q].state != R_FREE) ++q;
     if (q == sv->cfg.max_slots) return HAC_EBUSY;
@@ -291,7 +392,7 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     std::memset(&D, 0, sizeof D);
     Arena A;
     bind_zero(D, z, A, B);
-    bind_instance(D, *in, *p, z, 0, sv->ex, A, B);
+    bind_instance(D, *in, *p, z, 0, route ? sv->sex : sv->ex, A, B);
     std::vector<int2> rowmap(R.rows), slotmap(R.slots);
     for (int r = 0; r < R.rows; ++r) rowmap[r] = make_int2(0, r * ROWS_PER_BLOCK);
     for (int r = 0; r < R.slots; ++r) slotmap[r] = make_int2(0, r * SLOTS_PER_BLOCK);
@@ -316,6 +417,7 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     S.off = off;
     S.bytes = R.total;
     S.z = z;
+    S.route = route;
     S.t = 0;
     sv->zs[q] = z;
     *ticket = S.ticket;
@@ -329,7 +431,7 @@ int hac_server_tick(hac_server *sv)
     // also frees that tick's pinned order buffer)
     const int par = (int)(sv->ticks & 1);
     if (sv->tick_rec[par]) CK(cudaEventSynchronize(sv->tick_ev[par]));
-    std::vector<int> members;
+    std::vector<int> members, smembers;
     for (int q = 0; q < sv->cfg.max_slots; ++q) {
         Slot &S = sv->slots[q];
         if (S.state == R_PREP) {
@@ -339,7 +441,11 @@ int hac_server_tick(hac_server *sv)
             CK(cudaStreamWaitEvent(sv->stream, S.ready, 0));
             S.state = R_RUN;
         }
-        if (S.state == R_RUN && S.t < S.z.iters) members.push_back(q);
+        if (S.state == R_RUN && S.t < S.z.iters) (S.route ? smembers : members).push_back(q);
+    }
+    if (!smembers.empty()) {
+        int st = enqueue_step_route(sv, smembers, par);
+        if (st) return st;
     }
     if (!members.empty()) {
         std::vector<FusedGroup> groups;
@@ -368,6 +474,10 @@ int hac_server_tick(hac_server *sv)
             }
         }
         for (size_t r = 0; r < cnt; ++r) sv->slots[h_ord[r]].t += h_it[r];
+    }
+    if (!smembers.empty()) {
+        CK(cudaEventRecord(sv->sjoin, sv->sstream));
+        CK(cudaStreamWaitEvent(sv->stream, sv->sjoin, 0));
     }
     // stage the results of the requests that have reached their iteration count
     for (int q = 0; q < sv->cfg.max_slots; ++q) {
@@ -452,6 +562,10 @@ int hac_server_destroy(hac_server *sv)
         if (sv->join[g]) cudaEventDestroy(sv->join[g]);
     }
     for (int g = 0; g < 2; ++g) if (sv->tick_ev[g]) cudaEventDestroy(sv->tick_ev[g]);
+    if (sv->sstream) { cudaStreamSynchronize(sv->sstream); cudaStreamDestroy(sv->sstream); }
+    if (sv->sfork) cudaEventDestroy(sv->sfork);
+    if (sv->sjoin) cudaEventDestroy(sv->sjoin);
+    if (sv->h_sinst[0]) cudaFreeHost(sv->h_sinst[0]);
     if (sv->prep) cudaStreamDestroy(sv->prep);
     if (sv->pinned) cudaFreeHost(sv->pinned);
     delete sv;

@@ -56,7 +56,8 @@ class hac_exec(C.Structure):
 
 class hac_server_cfg(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("iters_per_tick", C.c_int32), ("max_n", C.c_int32),
-                ("steps_per_tick", C.c_int32), ("exec", hac_exec)]
+                ("steps_per_tick", C.c_int32), ("step_min_n", C.c_int32), ("step_ants_per_warp", C.c_int32),
+                ("step_warps_per_block", C.c_int32), ("exec", hac_exec)]
 
 
 _LIB = None
@@ -363,7 +364,8 @@ class Server:
     of `ws_bytes` bytes (a uint8 torch tensor)."""
 
     def __init__(self, ws_bytes: int, max_slots: int = 64, iters_per_tick: int = 10, max_n: int = 10000,
-                 exec_=None, stream=None, workspace=None, steps_per_tick: int = 0):
+                 exec_=None, stream=None, workspace=None, steps_per_tick: int = 0, step_min_n: int = 0,
+                 step_ants_per_warp: int = 1, step_warps_per_block: int = 8):
         import torch
         if not torch.cuda.is_available():
             raise HeatACOError(HAC_ECUDA, "no CUDA device")
@@ -371,7 +373,8 @@ class Server:
             workspace = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
         self.workspace = workspace
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        self.cfg = hac_server_cfg(max_slots, iters_per_tick, max_n, steps_per_tick,
+        self.cfg = hac_server_cfg(max_slots, iters_per_tick, max_n, steps_per_tick, step_min_n,
+                                  step_ants_per_warp, step_warps_per_block,
                                   exec_ if exec_ is not None else make_exec(fused=1))
         self.sizes = {}
         h = C.c_void_p()

@@ -106,17 +106,20 @@ def test_server_host_checks_before_cuda(lib):
     assert rb >= heataco.hac_batch_workspace_size([inst], [big]) - 4096
     h = C.c_void_p()
     dummy = C.c_void_p(256)          # never dereferenced: the checks fail first
-    for cfg in (heataco.hac_server_cfg(0, 1, 100, 0, heataco.make_exec()),
-                heataco.hac_server_cfg(4, 0, 100, 0, heataco.make_exec()),
-                heataco.hac_server_cfg(4, 1, 2, 0, heataco.make_exec()),
-                heataco.hac_server_cfg(4, 1, 70000, 0, heataco.make_exec()),
-                heataco.hac_server_cfg(4, 1, 100, 0, heataco.make_exec(ants_per_warp=1)),
-                heataco.hac_server_cfg(4, 1, 100, 0, heataco.make_exec(fallback_list=7)),
-                heataco.hac_server_cfg(4, 1, 100, -1, heataco.make_exec())):
+    for cfg in (heataco.hac_server_cfg(0, 1, 100, 0, 0, 0, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 0, 100, 0, 0, 0, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 2, 0, 0, 0, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 70000, 0, 0, 0, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 100, 0, 0, 0, 0, heataco.make_exec(ants_per_warp=1)),
+                heataco.hac_server_cfg(4, 1, 100, 0, 0, 0, 0, heataco.make_exec(fallback_list=7)),
+                heataco.hac_server_cfg(4, 1, 100, -1, 0, 0, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 100, 0, -5, 0, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 100, 0, 50, 3, 0, heataco.make_exec()),
+                heataco.hac_server_cfg(4, 1, 100, 0, 50, 1, 9, heataco.make_exec())):
         assert lib.hac_server_create(C.byref(cfg), dummy, C.c_size_t(1 << 30), None, C.byref(h)) == \
             heataco.HAC_EINVAL
         assert not h.value
-    cfg = heataco.hac_server_cfg(4, 1, 100, 0, heataco.make_exec())
+    cfg = heataco.hac_server_cfg(4, 1, 100, 0, 0, 0, 0, heataco.make_exec())
     assert lib.hac_server_create(C.byref(cfg), dummy, C.c_size_t(4096), None, C.byref(h)) == heataco.HAC_ENOMEM
     assert lib.hac_server_create(None, dummy, C.c_size_t(1 << 30), None, C.byref(h)) == heataco.HAC_EINVAL
     for call in (lambda: lib.hac_server_tick(None), lambda: lib.hac_server_destroy(None),

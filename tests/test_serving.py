@@ -53,10 +53,12 @@ def _drain(srv, tickets, out, max_ticks=1000):
     raise AssertionError("requests did not finish")
 
 
-@pytest.mark.parametrize("apw,ipt,spt", [(4, 3, 0), (32, 5, 1500), (2, 4, 0)])
-def test_mix_equals_alone_and_oracle(hac, orc, apw, ipt, spt):
+@pytest.mark.parametrize("apw,ipt,spt,smin,sapw", [(4, 3, 0, 0, 1), (32, 5, 1500, 0, 1), (2, 4, 0, 0, 1),
+                                                   (4, 3, 1500, 300, 1), (32, 4, 0, 100, 2), (4, 5, 0, 3, 4)])
+def test_mix_equals_alone_and_oracle(hac, orc, apw, ipt, spt, smin, sapw):
     reqs = _requests()
     srv = hac.Server(64 << 20, max_slots=8, iters_per_tick=ipt, max_n=1000, steps_per_tick=spt,
+                     step_min_n=smin, step_ants_per_warp=sapw, step_warps_per_block=4 if sapw == 4 else 8,
                      exec_=hac.make_exec(ants_per_warp=apw, fused=1, fallback_list=32 if apw != 2 else 0))
     try:
         tickets, order, out = [], [], {}
