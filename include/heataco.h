@@ -245,7 +245,9 @@ int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count
  * own iteration, in the persistent cluster kernel (hac_exec.fused).  A request
  * returns the same tour and length as hac_solve on the same instance and
  * parameters, alone or in any mix.  Inputs are host pointers; the server
- * copies them during hac_server_submit, so the caller may reuse them at once.
+ * copies them (into its pinned upload ring, or for a request larger than the
+ * ring straight to the device) during hac_server_submit, so the caller may
+ * reuse them at once.
  * A server is not thread-safe: call it from one host thread at a time.
  *
  *   max_slots       requests resident at once (1..4096)
@@ -287,7 +289,8 @@ int hac_server_request_bytes(const hac_instance *in, const hac_params *p, size_t
  * pinned host staging of about max_slots * (4 * max_n + 512) bytes (and,
  * with step_min_n > 0, per-tick work tables of about max_slots * (16 KB +
  * max_n / 4) bytes, twice, on both sides), one side stream for preparation,
- * three for concurrent cluster-size groups and one for the per-step route.
+ * three for concurrent cluster-size groups and one for the per-step route,
+ * four preparation streams and a pinned upload ring of 64 MB.
  * HAC_ENOMEM if the workspace cannot hold the header and a minimal heap. */
 int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_bytes, void *stream,
                       hac_server **out);
@@ -295,7 +298,8 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
 /* Admits a request: checks it (as hac_batch_create does for host inputs),
  * takes a free slot and the first heap region that fits, uploads the inputs
  * and enqueues the preparation (Sec. III-A: candidate lists, evidence, kappa,
- * W; T_NN and the bounds) on the preparation stream.  Returns a ticket > 0.
+ * W; T_NN and the bounds) on the next preparation stream.  Does not wait for
+ * the device unless the upload ring is full.  Returns a ticket > 0.
  * HAC_EBUSY when no slot or no region is free (retry after polling finished
  * requests); HAC_EINVAL for n > max_n or a malformed request;
  * HAC_EUNSUPPORTED when a request routed to the cluster kernel does not fit

@@ -9,9 +9,11 @@
 //
 //   submit: checks the request, finds a free slot and a heap region (first
 //           fit; HAC_EBUSY when either is missing, so admission follows free
-//           memory), uploads the inputs and runs the preparation kernels
-//           (candidate lists, evidence, kappa, W, T_NN, bounds, tau_0) on a
-//           side stream, so that preparation overlaps the running iterations.
+//           memory), stages the inputs in a pinned upload ring, copies them
+//           and runs the preparation kernels (candidate lists, evidence,
+//           kappa, W, T_NN, bounds, tau_0) on one of PREP_STREAMS side
+//           streams, so that preparations overlap each other and the running
+//           iterations, and submit returns without waiting for the device.
 //   tick:   admits the requests whose preparation has finished, then runs
 //           the tick's MMAS iterations of every admitted request.  Requests
 //           below step_min_n nodes run in one launch of the persistent
@@ -30,6 +32,7 @@
 // decodes to the same tour alone and in any mix.
 #include <algorithm>
 #include <cstring>
+#include <deque>
 #include <new>
 #include <vector>
 
@@ -41,6 +44,14 @@ using namespace hac::host;
 namespace {
 
 enum ReqState { R_FREE = 0, R_PREP, R_RUN, R_RETIRE };
+
+constexpr int PREP_STREAMS = 4;
+constexpr size_t RING_BYTES = (size_t)64 << 20;   // pinned upload ring
+
+struct RingEntry {
+    size_t off, bytes;
+    cudaEvent_t ev;                 // the copies out of this entry are done
+};
 
 struct Slot {
     int state = R_FREE;
@@ -85,7 +96,13 @@ Region region_of(const Sizes &z)
 struct hac_server {
     hac_server_cfg cfg{};
     hac_exec ex{};
-    cudaStream_t stream = nullptr, prep = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t prep[PREP_STREAMS] = {};
+    int next_prep = 0;
+    char *ring = nullptr;           // pinned, RING_BYTES
+    size_t ring_head = 0;
+    std::deque<RingEntry> ring_q;   // live entries, oldest first
+    std::vector<cudaEvent_t> ring_ev;   // idle events
     DevInst *d_inst = nullptr;
     int32_t *d_order[2] = {nullptr, nullptr};   // alternating per tick
     int32_t *d_iters[2] = {nullptr, nullptr};   // iterations of each cluster this tick
@@ -209,6 +226,72 @@ int enqueue_groups(hac_server *sv, std::vector<FusedGroup> &groups, const int32_
     cudaError_t e = launch_groups(sv->d_inst, d_order, d_iters, groups, sv->ex.ants_per_warp, 0, sv->stream);
     if (e != cudaSuccess) { g_last_cuda = (int)e; return HAC_ECUDA; }
     sv->launches += (long long)groups.size();
+    return HAC_OK;
+}
+
+// Reserves `bytes` of the upload ring (bytes <= RING_BYTES), waiting for the
+// oldest entries' copies when it is full.  Entries are taken in ring order.
+int ring_take(hac_server *sv, size_t bytes, size_t &off)
+{
+    auto overlaps = [&](size_t pos) {
+        for (const RingEntry &r : sv->ring_q)
+            if (pos < r.off + r.bytes && r.off < pos + bytes) return true;
+        return false;
+    };
+    for (;;) {
+        if (sv->ring_q.empty()) sv->ring_head = 0;
+        const size_t pos = sv->ring_head + bytes <= RING_BYTES ? sv->ring_head : 0;
+        if (!overlaps(pos)) {
+            off = pos;
+            sv->ring_head = pos + bytes;
+            return HAC_OK;
+        }
+        RingEntry r = sv->ring_q.front();
+        CK(cudaEventSynchronize(r.ev));
+        sv->ring_q.pop_front();
+        sv->ring_ev.push_back(r.ev);
+    }
+}
+
+// Host -> device copies of one request (inputs, work tables, DevInst) through
+// the pinned ring on stream ps; falls back to plain copies from the caller's
+// memory when the request is larger than the ring.
+struct Upload {
+    const void *src;
+    void *dst;
+    size_t bytes;
+};
+
+int upload_staged(hac_server *sv, const std::vector<Upload> &ups, cudaStream_t ps)
+{
+    size_t total = 0;
+    for (const Upload &u : ups) total += (u.bytes + 15) & ~(size_t)15;
+    if (total > RING_BYTES) {
+        for (const Upload &u : ups)
+            if (u.bytes) CK(cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, ps));
+        return HAC_OK;
+    }
+    // retire finished entries first, then reserve
+    while (!sv->ring_q.empty() && cudaEventQuery(sv->ring_q.front().ev) == cudaSuccess) {
+        sv->ring_ev.push_back(sv->ring_q.front().ev);
+        sv->ring_q.pop_front();
+    }
+    size_t off;
+    int st = ring_take(sv, total, off);
+    if (st) return st;
+    cudaEvent_t ev;
+    if (!sv->ring_ev.empty()) { ev = sv->ring_ev.back(); sv->ring_ev.pop_back(); }
+    else CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    size_t o = off;
+    for (const Upload &u : ups) {
+        if (u.bytes) {
+            std::memcpy(sv->ring + o, u.src, u.bytes);
+            CK(cudaMemcpyAsync(u.dst, sv->ring + o, u.bytes, cudaMemcpyHostToDevice, ps));
+        }
+        o += (u.bytes + 15) & ~(size_t)15;
+    }
+    CK(cudaEventRecord(ev, ps));
+    sv->ring_q.push_back(RingEntry{off, total, ev});
     return HAC_OK;
 }
 
@@ -355,7 +438,9 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
         if ((e = cudaEventCreateWithFlags(&S.ready, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
         if ((e = cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
     }
-    if ((e = cudaStreamCreateWithFlags(&sv->prep, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    for (int g = 0; g < PREP_STREAMS; ++g)
+        if ((e = cudaStreamCreateWithFlags(&sv->prep[g], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+    if ((e = cudaHostAlloc((void **)&sv->ring, RING_BYTES, cudaHostAllocDefault)) != cudaSuccess) return fail(e);
     for (int g = 0; g < 3; ++g) {
         if ((e = cudaStreamCreateWithFlags(&sv->side[g], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
         if ((e = cudaEventCreateWithFlags(&sv->fork[g], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
@@ -364,7 +449,8 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
     for (int g = 0; g < 2; ++g)
         if ((e = cudaEventCreateWithFlags(&sv->tick_ev[g], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
     // the preparation kernels are the ones that report into the error word
-    if ((e = cudaMemsetAsync(sv->d_err, 0, sizeof(int), sv->prep)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(sv->d_err, 0, sizeof(int), sv->prep[0])) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(sv->prep[0])) != cudaSuccess) return fail(e);
     *out = sv;
     return HAC_OK;
 }
@@ -397,17 +483,26 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     for (int r = 0; r < R.rows; ++r) rowmap[r] = make_int2(0, r * ROWS_PER_BLOCK);
     for (int r = 0; r < R.slots; ++r) slotmap[r] = make_int2(0, r * SLOTS_PER_BLOCK);
     int2 *d_rowmap = (int2 *)(B + R.rowmap), *d_slotmap = (int2 *)(B + R.slotmap);
-    cudaStream_t ps = sv->prep;
+    cudaStream_t ps = sv->prep[sv->next_prep];
     auto undo = [&](int code) {
         heap_free(sv, off, R.total);
         return code;
     };
     if (cudaMemsetAsync(B, 0, R.zero_end, ps) != cudaSuccess) return undo(HAC_ECUDA);
-    if ((st = upload_inputs(D, *in, z, ps))) return undo(st);
-    if (cudaMemcpyAsync(d_rowmap, rowmap.data(), rowmap.size() * sizeof(int2), cudaMemcpyHostToDevice, ps) ||
-        cudaMemcpyAsync(d_slotmap, slotmap.data(), slotmap.size() * sizeof(int2), cudaMemcpyHostToDevice, ps) ||
-        cudaMemcpyAsync(sv->d_inst + q, &D, sizeof(DevInst), cudaMemcpyHostToDevice, ps))
-        return undo(HAC_ECUDA);
+    std::vector<Upload> ups;
+    const size_t n = z.n, nnz = (size_t)z.nnz;
+    if (z.kind == 0) ups.push_back(Upload{in->coords, (void *)D.xy, n * 8});
+    else ups.push_back(Upload{in->cost, (void *)D.cost, n * n * 4});
+    ups.push_back(Upload{in->h_rowptr, (void *)D.rowptr, (n + 1) * 4});
+    if (nnz) {
+        ups.push_back(Upload{in->h_col, (void *)D.col, nnz * 4});
+        ups.push_back(Upload{in->h_val, (void *)D.val, nnz * (z.half ? 2 : 4)});
+    }
+    ups.push_back(Upload{rowmap.data(), d_rowmap, rowmap.size() * sizeof(int2)});
+    ups.push_back(Upload{slotmap.data(), d_slotmap, slotmap.size() * sizeof(int2)});
+    ups.push_back(Upload{&D, sv->d_inst + q, sizeof(DevInst)});
+    if ((st = upload_staged(sv, ups, ps))) return undo(st);
+    sv->next_prep = (sv->next_prep + 1) % PREP_STREAMS;
     sv->launches += launch_prep(sv->d_inst + q, &D, 1, d_rowmap, R.rows, d_slotmap, R.slots, sv->d_err, ps);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(S.ready, ps);
@@ -530,7 +625,7 @@ int hac_server_stats(hac_server *sv, int32_t *resident, int32_t *finished, size_
     if (finished) *finished = fin;
     if (free_bytes) *free_bytes = free_total(sv);
     if (device_error) {
-        CK(cudaStreamSynchronize(sv->prep));
+        for (int g = 0; g < PREP_STREAMS; ++g) CK(cudaStreamSynchronize(sv->prep[g]));
         CK(cudaStreamSynchronize(sv->stream));
         int err = 0;
         CK(cudaMemcpy(&err, sv->d_err, sizeof err, cudaMemcpyDeviceToHost));
@@ -549,7 +644,7 @@ int hac_server_launches(hac_server *sv, int64_t *launches)
 int hac_server_destroy(hac_server *sv)
 {
     if (!sv) return HAC_EINVAL;
-    if (sv->prep) cudaStreamSynchronize(sv->prep);
+    for (int g = 0; g < PREP_STREAMS; ++g) if (sv->prep[g]) cudaStreamSynchronize(sv->prep[g]);
     for (int g = 0; g < 3; ++g) if (sv->side[g]) cudaStreamSynchronize(sv->side[g]);
     cudaStreamSynchronize(sv->stream);
     for (Slot &S : sv->slots) {
@@ -566,7 +661,10 @@ int hac_server_destroy(hac_server *sv)
     if (sv->sfork) cudaEventDestroy(sv->sfork);
     if (sv->sjoin) cudaEventDestroy(sv->sjoin);
     if (sv->h_sinst[0]) cudaFreeHost(sv->h_sinst[0]);
-    if (sv->prep) cudaStreamDestroy(sv->prep);
+    for (int g = 0; g < PREP_STREAMS; ++g) if (sv->prep[g]) cudaStreamDestroy(sv->prep[g]);
+    for (const RingEntry &r : sv->ring_q) cudaEventDestroy(r.ev);
+    for (cudaEvent_t ev : sv->ring_ev) cudaEventDestroy(ev);
+    if (sv->ring) cudaFreeHost(sv->ring);
     if (sv->pinned) cudaFreeHost(sv->pinned);
     delete sv;
     return HAC_OK;

@@ -143,3 +143,23 @@ def test_atsp_request_alone_in_server(hac, orc):
     o = orc.Oracle(inst, p).iterate(p.iterations)
     assert np.array_equal(out[t][0], o.get("gb_tour"))
     assert out[t][1] == o.scalars()["L_gb"]
+
+
+def test_upload_ring_wraps_without_corrupting_inputs(hac):
+    # 24 ATSP requests of ~4.3 MB of inputs each: more than the 64 MB pinned
+    # upload ring, so submission wraps around it and waits for earlier copies
+    insts = [synth.atsp_instance(300 + q, 1000, K=20) for q in range(24)]
+    ps = [synth.Params(m=8, k=8, iterations=2, rho=0.2, degree_target=1, seed=300 + q) for q in range(24)]
+    srv = hac.Server(1 << 30, max_slots=32, iters_per_tick=1, max_n=1000, exec_=hac.make_exec(fused=1),
+                     step_min_n=900)
+    try:
+        tickets = [srv.submit(i, p) for i, p in zip(insts, ps)]
+        assert all(t is not None for t in tickets)
+        out = {}
+        _drain(srv, list(tickets), out)
+    finally:
+        srv.close()
+    for t, i, p in zip(tickets, insts, ps):
+        ref_t, ref_l = hac.solve(i, p)
+        assert np.array_equal(out[t][0], ref_t)
+        assert out[t][1] == ref_l
