@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--plain-sample", type=int, default=4,
                     help="instances decoded one per launch sequence for the plain-GPU comparison (0: skip)")
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count (profiling)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick the execution layout with hac_batch_autotune before the warm-up (untimed); "
+                         "0: use --apw/--wpb/--fused/--fbl/--clog as given")
+    ap.add_argument("--tune-iters", type=int, default=10, help="iterations timed per autotuner candidate")
     ap.add_argument("--requests", type=int, default=400, help="serve: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrival rate (req/s)")
     ap.add_argument("--steps-per-tick", type=int, default=4000, help="serve: construction steps per ant per tick")
@@ -271,15 +275,26 @@ def run_ours(args):
     steps_per = total_ant_steps(insts, ps)
     alg_bytes = algorithmic_construct_bytes(insts, ps)
     stream = torch.cuda.Stream()
-    ex = heataco.make_exec(args.apw, args.wpb, use_graph=0, profile=1, fused=args.fused,
-                           fallback_list=args.fbl, cluster_log2=args.clog)
-    kgroup = 3 if args.fused else 0
-
     dins = device_instances(insts, torch)
     m = heataco._Marshal(dins, ps, True)
     ws_bytes = C.c_size_t(0)
     heataco._check(L.hac_batch_workspace_size(m.ins, m.ps, count, 1, C.byref(ws_bytes)), "size")
     ws = torch.empty(ws_bytes.value, dtype=torch.uint8, device="cuda")
+
+    tune = None
+    if args.autotune:
+        best, ms_it = heataco.hac_exec(), C.c_double(0)
+        t0 = time.perf_counter()
+        heataco._check(L.hac_batch_autotune(m.ins, m.ps, count, 1, C.c_void_p(ws.data_ptr()), ws_bytes,
+                                            args.tune_iters, C.c_void_p(stream.cuda_stream), C.byref(best),
+                                            C.byref(ms_it)), "autotune")
+        tune = {"seconds": time.perf_counter() - t0, "trial_iters": args.tune_iters,
+                "ms_per_iter": ms_it.value}
+        args.apw, args.wpb, args.fused = best.ants_per_warp, best.warps_per_block, best.fused
+        args.fbl, args.clog = best.fallback_list, best.cluster_log2
+    ex = heataco.make_exec(args.apw, args.wpb, use_graph=0, profile=1, fused=args.fused,
+                           fallback_list=args.fbl, cluster_log2=args.clog)
+    kgroup = 3 if args.fused else 0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
     def one_step():
@@ -441,7 +456,9 @@ def run_ours(args):
                        "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
                        "inputs": "resident in HBM before the timed region",
                        "ants_per_warp": ex.ants_per_warp or 4, "fused": args.fused,
-                       "fallback_list": args.fbl, "kernel_timing": "CUDA events per launch"},
+                       "warps_per_block": args.wpb, "cluster_log2": args.clog,
+                       "fallback_list": args.fbl, "autotune": tune,
+                       "kernel_timing": "CUDA events per launch"},
             "instances_per_s": inst_per_s,
             "e2e": e2e,
             "plain_gpu": plain,
