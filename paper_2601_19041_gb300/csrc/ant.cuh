@@ -36,15 +36,23 @@ __device__ __forceinline__ int int_of(const int4 &v, int w)
     return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
 }
 
-// candidate rows in global memory (int32 ids, FP32 choice)
+// Candidate rows hand out padding slots as node n: the construction presets
+// bit n of every visited mask, so a padding slot is never live and no slot
+// needs a validity test of its own.
+
+// candidate rows in global memory (int32 ids, -1 on padding; FP32 choice)
 struct GlobalRows {
     const int4 *cand4;
     const float4 *ch4;
-    int G;
+    int G, n;
     __device__ __forceinline__ void load(int cur, int g, int4 &id, float4 &ch) const
     {
         id = __ldg(cand4 + (size_t)cur * G + g);
         ch = __ldg(ch4 + (size_t)cur * G + g);
+        id.x = id.x < 0 ? n : id.x;
+        id.y = id.y < 0 ? n : id.y;
+        id.z = id.z < 0 ? n : id.z;
+        id.w = id.w < 0 ? n : id.w;
     }
 };
 
@@ -89,7 +97,7 @@ __device__ __forceinline__ float4 ld_smem_f4(uint32_t a)
 
 // candidate rows in the shared memory of the CTAs of a cluster, interleaved by
 // row (row i lives in CTA i & (C-1) at local row i >> CLOG); uint16 ids with
-// 0xffff for padding.  Same layout (and offsets) in every CTA.
+// n for padding.  Same layout (and offsets) in every CTA.
 template <int CLOG>
 struct ClusterRows {
     uint32_t idx_base, ch_base;   // shared-window addresses in the calling CTA
@@ -108,11 +116,10 @@ struct ClusterRows {
             raw = ld_dsmem_u2(map_to_rank(ia, owner));
             chv = ld_dsmem_f4(map_to_rank(ca, owner));
         }
-        const int a0 = raw.x & 0xffff, a1 = raw.x >> 16, a2 = raw.y & 0xffff, a3 = raw.y >> 16;
-        id.x = a0 == 0xffff ? -1 : a0;
-        id.y = a1 == 0xffff ? -1 : a1;
-        id.z = a2 == 0xffff ? -1 : a2;
-        id.w = a3 == 0xffff ? -1 : a3;
+        id.x = (int)(raw.x & 0xffffu);
+        id.y = (int)(raw.x >> 16);
+        id.z = (int)(raw.y & 0xffffu);
+        id.w = (int)(raw.y >> 16);
     }
 };
 
@@ -164,13 +171,16 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
     const int nwords = (n + 31) >> 5;
     unsigned *vis = vis_warp + seg * stride;
 
-    for (int w = sl; w < nwords; w += SEG) vis[w] = 0u;
+    for (int w = sl; w <= (n >> 5); w += SEG) vis[w] = 0u;   // bits 0..n
     __syncwarp();
 
     uint32_t qbase = 0;
     U4 rnd = draw_block(seed, (uint32_t)t, (uint32_t)(real ? a : 0), (uint32_t)sl);
     const int start = (int)__umulhi(__shfl_sync(FULL_MASK, rnd.x, segbase), (uint32_t)n);
-    if (sl == 0 && real) vis[start >> 5] |= 1u << (start & 31);
+    if (sl == 0) {
+        vis[n >> 5] |= 1u << (n & 31);                       // padding node: never live
+        if (real) vis[start >> 5] |= 1u << (start & 31);
+    }
     __syncwarp();
     int tb = sl == 0 ? start : 0;                  // step s of the tour / slot at lane s % SEG
     unsigned sb8 = 0xffu;
@@ -180,7 +190,7 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
     int nfb = 0;
     int cur = start;
     // the row of the current node is loaded at the end of the previous step
-    int4 id = make_int4(-1, -1, -1, -1);
+    int4 id = make_int4(n, n, n, n);
     float4 ch = make_float4(0.f, 0.f, 0.f, 0.f);
     if (real && sl < G) rows.load(cur, sl, id, ch);
 
@@ -193,7 +203,7 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
         }
         const uint32_t x = __shfl_sync(FULL_MASK, word_of(rnd, s & 3), (int)(q - qbase), SEG);
 
-        auto unv = [&](int j) { return j >= 0 && !((vis[j >> 5] >> (j & 31)) & 1u); };
+        auto unv = [&](int j) { return !((vis[j >> 5] >> (j & 31)) & 1u); };
         const float w0 = unv(id.x) ? ch.x : 0.0f;
         const float w1 = unv(id.y) ? ch.y : 0.0f;
         const float w2 = unv(id.z) ? ch.z : 0.0f;
@@ -205,12 +215,13 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
             const float v = __shfl_up_sync(FULL_MASK, inc, o, 8);
             if ((lane & 7) >= o) inc = __fadd_rn(inc, v);
         }
-        const float ex = __shfl_up_sync(FULL_MASK, inc, 1, 8);
-        const bool g0 = (lane & 7) == 0;
-        const float S0 = g0 ? p0 : __fadd_rn(ex, p0);
-        const float S1 = g0 ? p1 : __fadd_rn(ex, p1);
-        const float S2 = g0 ? p2 : __fadd_rn(ex, p2);
-        const float S3 = g0 ? p3 : __fadd_rn(ex, p3);
+        // exclusive prefix; +0 for the first group leaves p_c unchanged (p_c >= 0)
+        const float exu = __shfl_up_sync(FULL_MASK, inc, 1, 8);
+        const float ex = (lane & 7) == 0 ? 0.0f : exu;
+        const float S0 = __fadd_rn(ex, p0);
+        const float S1 = __fadd_rn(ex, p1);
+        const float S2 = __fadd_rn(ex, p2);
+        const float S3 = __fadd_rn(ex, p3);
         const float total = __shfl_sync(FULL_MASK, inc, 7, SEG);
         const float r = __fmul_rn(unif24(x), total);
 
@@ -222,11 +233,15 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
         // an idle segment (no ant) counts as decided
         const unsigned hit_all = __ballot_sync(FULL_MASK, hq >= 0 || (!real && sl == 0));
         const unsigned hit_bits = (hit_all >> segbase) & SEGMASK;
-        // segments without a hit (no live slot, or the rounding corner case)
-        unsigned nohit = 0u;
-#pragma unroll
-        for (int g = 0; g < APW; ++g)
-            if (!((hit_all >> (g * SEG)) & SEGMASK)) nohit |= 1u << (g * SEG);
+        // segments without a hit (no live slot, or the rounding corner case):
+        // the top bit of every all-zero SEG-bit field (exact per field, no
+        // carries between fields)
+        unsigned nohit;
+        if (SEG == 32) nohit = hit_all == 0u;
+        else {
+            constexpr unsigned LOW = SEG == 16 ? 0x7fff7fffu : SEG == 8 ? 0x7f7f7f7fu : 0u;
+            nohit = ~(((hit_all & LOW) + LOW) | hit_all | LOW);
+        }
         int src, myq;
         bool live = true;
         unsigned need = 0u;

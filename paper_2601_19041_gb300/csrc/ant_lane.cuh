@@ -44,7 +44,8 @@ __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &r
     int32_t *__restrict__ fbs = I.fbs + (size_t)(real ? a : 0) * n;
     int nfb = 0;
 
-    for (int w = 0; w < nwords; ++w) vis_warp[w * 32 + lane] = 0u;
+    for (int w = 0; w <= (n >> 5); ++w) vis_warp[w * 32 + lane] = 0u;   // bits 0..n
+    vis_warp[(n >> 5) * 32 + lane] |= 1u << (n & 31);                   // padding node n: never live
     U4 rnd = draw_block(seed, (uint32_t)t, (uint32_t)(real ? a : 0), 0u);
     const int start = (int)__umulhi(rnd.x, (uint32_t)n);
     int cur = start;
@@ -59,7 +60,7 @@ __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &r
         int id[4 * NG];
 #pragma unroll
         for (int g = 0; g < NG; ++g) {
-            int4 i4 = make_int4(-1, -1, -1, -1);
+            int4 i4 = make_int4(n, n, n, n);
             float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (real && g < G) rows.load(cur, g, i4, c4);
             id[4 * g] = i4.x; id[4 * g + 1] = i4.y; id[4 * g + 2] = i4.z; id[4 * g + 3] = i4.w;
@@ -73,7 +74,7 @@ __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &r
             for (int q = 0; q < 4; ++q) {
                 const int c = 4 * g + q;
                 const int j = id[c];
-                const bool u = j >= 0 && !((vis_warp[(j >> 5) * 32 + lane] >> (j & 31)) & 1u);
+                const bool u = !((vis_warp[(j >> 5) * 32 + lane] >> (j & 31)) & 1u);
                 w[c] = u ? w[c] : 0.0f;
                 bits |= (w[c] > 0.0f ? 1u : 0u) << q;
             }

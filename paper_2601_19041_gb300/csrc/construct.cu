@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256, 1) k_construct(const DevInst *__restrict_
     const int t = I.st->t;
     if (t >= I.iters) return;                       // warp-uniform
     GlobalRows rows{reinterpret_cast<const int4 *>(I.cand), reinterpret_cast<const float4 *>(I.choice),
-                    I.k_pad >> 2};
+                    I.k_pad >> 2, I.n};
     build_tours<APW>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m, smem_vis + (size_t)wib * APW * nwords_max,
                      nwords_max, reinterpret_cast<const float2 *>(I.xy));
 }
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256, 1) k_construct_lane(const DevInst *__rest
     const int t = I.st->t;
     if (t >= I.iters) return;
     GlobalRows rows{reinterpret_cast<const int4 *>(I.cand), reinterpret_cast<const float4 *>(I.choice),
-                    I.k_pad >> 2};
+                    I.k_pad >> 2, I.n};
     build_tours_lane<NG>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m, smem_vis + (size_t)wib * 32 * nwords_max,
                          reinterpret_cast<const float2 *>(I.xy));
 }
@@ -58,7 +58,7 @@ template <int APW>
 static void launch_construct_apw(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len,
                                  int warps_per_block, int max_n, cudaStream_t s)
 {
-    int nwords = (max_n + 31) / 32;
+    int nwords = (max_n + 32) / 32;   // visited bits 0..n (n: padding id)
     size_t smem = (size_t)warps_per_block * APW * nwords * sizeof(unsigned);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_construct<APW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -72,7 +72,7 @@ int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_l
                      int warps_per_block, int max_n, int max_kp, int count, cudaStream_t s)
 {
     if (apw == 32) {
-        const int nwords = (max_n + 31) / 32;
+        const int nwords = (max_n + 32) / 32;
         const size_t smem = (size_t)warps_per_block * 32 * nwords * sizeof(unsigned);
         const int blocks = (warpmap_len + warps_per_block - 1) / warps_per_block;
         const int G = max_kp / 4;

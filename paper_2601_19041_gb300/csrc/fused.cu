@@ -1,7 +1,8 @@
 // Persistent fused iteration kernel: one thread-block cluster per instance runs
 // whole MMAS iterations (Algorithm 1 lines 9-19) without leaving the GPU.
 //
-// Per instance the candidate table C_i (uint16 ids) and choice_info (FP32)
+// Per instance the candidate table C_i (uint16 ids, padding slots hold n) and
+// choice_info (FP32)
 // live in the shared memory of the cluster's C CTAs, interleaved by row (row
 // i in CTA i mod C).  Every construction step reads its row from local shared
 // memory or, through the cluster's distributed shared memory, from a
@@ -76,10 +77,10 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
         const int i = rank + (l << CLOG);
         if (i < n) {
             const int j = I.cand[(size_t)i * kp + c];
-            sidx[e] = j < 0 ? (uint16_t)0xffff : (uint16_t)j;
+            sidx[e] = (uint16_t)(j < 0 ? n : j);   // padding: node n, whose visited bit is preset
             sch[e] = I.choice[(size_t)i * kp + c];
         } else {
-            sidx[e] = 0xffff;
+            sidx[e] = (uint16_t)n;
             sch[e] = 0.0f;
         }
     }
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
         const float tmin = st->tau_min, tmax = st->tau_max;
         for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
             const int j = sidx[e];
-            if (j == 0xffff) continue;
+            if (j >= n) continue;   // padding
             const int l = e / kp, c = e - l * kp;
             const int i = rank + (l << CLOG);
             sch[e] = update_slot(I, (size_t)i * kp + c, i, j, omega, delta, tmin, tmax);

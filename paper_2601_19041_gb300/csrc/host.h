@@ -315,7 +315,7 @@ inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &mem
         const int apc = (z.m + C - 1) / C;
         warps = (apc + apw - 1) / apw;
         if (warps > 16) return false;   // k_fused is compiled for at most 512 threads
-        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 31) / 32, 0, 0) <= FUSED_SMEM_LIMIT;
+        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 32) / 32, 0, 0) <= FUSED_SMEM_LIMIT;
     };
     for (int q = 0; q < count; ++q) {
         if (zs[members[q]].n > 65534) return HAC_EUNSUPPORTED;
@@ -338,7 +338,7 @@ inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &mem
                 G.count++;
                 G.rows_cap = std::max(G.rows_cap, rows);
                 G.kp_cap = std::max(G.kp_cap, z.kp);
-                G.stride = std::max(G.stride, (z.n + 31) / 32);
+                G.stride = std::max(G.stride, (z.n + 32) / 32);   // bits 0..n (n: padding)
                 G.warps = std::max(G.warps, warps);
             }
             if (!G.count) continue;
