@@ -288,7 +288,7 @@ static int enqueue_iteration(hac_batch *bt)
     });
     k += timed(bt, 1, [&] {
         return launch_iteration_tail(bt->d_inst, bt->count, bt->d_slotmap, bt->slotmap_len,
-                                     bt->any_ls, bt->stream);
+                                     bt->any_ls, bt->max_n, bt->stream);
     });
     return k;
 }

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
             block_iteration_best(I, st);
             if (I.local_search) {
                 if (wib == 0) {
-                    warp_two_opt(I, I.ib_tour);
+                    warp_two_opt(I, I.ib_tour, ls_global(I, I.ib_tour));
                     const double L = warp_tour_length(I, I.ib_tour);
                     if (lane == 0) st->L_ib = L;
                 }

@@ -156,7 +156,9 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
     if (z.ls) {
         put("nbr", A.take(n * z.ls_k * 4));
         put("nbrd", A.take(n * z.ls_k * 8));
+        put("nbrd32", A.take(n * z.ls_k * 4));
         put("ls_pos", A.take(n * 4));
+        put("ls_el", A.take(n * 4));
         put("ls_dlb", A.take(n));
     }
     put("fbl", A.take(n * FBL_LEN * 4));
@@ -267,6 +269,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
         SETP(evid, double *) SETP(logev, double *) SETP(base, double *) SETP(W, float *)
         SETP(tau, float *) SETP(choice, float *) SETP(nbr, int32_t *) SETP(nbrd, double *)
         SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
+        SETP(nbrd32, float *) SETP(ls_el, float *)
         SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *)
         SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
         SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)

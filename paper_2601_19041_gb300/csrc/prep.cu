@@ -644,6 +644,7 @@ __global__ void k_nbr(const DevInst *insts, const int2 *rowmap)
     if (lane < I.ls_k) {
         I.nbr[(size_t)a * I.ls_k + lane] = j;
         I.nbrd[(size_t)a * I.ls_k + lane] = d;
+        I.nbrd32[(size_t)a * I.ls_k + lane] = __double2float_rn(d);
     }
 }
 
@@ -809,7 +810,7 @@ __global__ void k_init_tau(const DevInst *insts, const int2 *slotmap)
 }
 
 // defined in twoopt.cu
-void launch_two_opt_nn(const DevInst *d_inst, int count, cudaStream_t s);
+void launch_two_opt_nn(const DevInst *d_inst, int count, int max_n, cudaStream_t s);
 
 int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const int2 *d_rowmap,
                 int rowmap_len, const int2 *d_slotmap, int slotmap_len, int *d_err,
@@ -842,7 +843,7 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
     if (any_ls) { k_nbr<<<rowmap_len, threads, 0, s>>>(d_inst, d_rowmap); ++launched; }
     size_t vis_bytes = (size_t)((max_n + 31) / 32) * 4;
     k_nn_tour<<<count, 1024, vis_bytes, s>>>(d_inst);
-    if (any_ls) { launch_two_opt_nn(d_inst, count, s); ++launched; }
+    if (any_ls) { launch_two_opt_nn(d_inst, count, max_n, s); ++launched; }
     k_init_bounds<<<count, 256, 0, s>>>(d_inst);
     k_fbl_check<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
     const int wpw = (max_n + 31) / 32;

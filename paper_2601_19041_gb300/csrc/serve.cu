@@ -329,7 +329,8 @@ int enqueue_step_route(hac_server *sv, const std::vector<int> &mem, int par)
     for (int q = 0; q < it; ++q) {
         sv->launches += launch_construct(sv->d_sinst[par], sv->d_swarp[par], (int)nw, apw,
                                          sv->sex.warps_per_block, max_n, max_kp, count, ss);
-        sv->launches += launch_iteration_tail(sv->d_sinst[par], count, sv->d_sslot[par], (int)ns, any_ls, ss);
+        sv->launches += launch_iteration_tail(sv->d_sinst[par], count, sv->d_sslot[par], (int)ns, any_ls, max_n,
+                                              ss);
     }
     CK(cudaGetLastError());
     for (int q : mem) sv->slots[q].t += it;

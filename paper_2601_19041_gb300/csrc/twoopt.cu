@@ -1,34 +1,54 @@
-// 2-opt kernels (one warp per instance); the search itself is in twoopt.cuh.
+// 2-opt kernels (one warp per instance, its arrays in shared memory when they
+// fit); the search itself is in twoopt.cuh.
 #include "twoopt.cuh"
 
 namespace hac {
 
-__global__ void k_two_opt_nn(const DevInst *insts)
+__global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
 {
+    extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x];
     if (!I.local_search) return;
-    warp_two_opt(I, I.nn_tour);
+    warp_two_opt(I, I.nn_tour, ls_shared(I, I.nn_tour, ls_sm, smem_bytes));
     const double L = warp_tour_length(I, I.nn_tour);
     if (threadIdx.x == 0) I.st->L_nn = L;
 }
 
-__global__ void k_two_opt_ib(const DevInst *insts)
+__global__ void k_two_opt_ib(const DevInst *insts, unsigned smem_bytes)
 {
+    extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x];
     if (!I.local_search || !I.st->active) return;
-    warp_two_opt(I, I.ib_tour);
+    warp_two_opt(I, I.ib_tour, ls_shared(I, I.ib_tour, ls_sm, smem_bytes));
     const double L = warp_tour_length(I, I.ib_tour);
     if (threadIdx.x == 0) I.st->L_ib = L;
 }
 
-void launch_two_opt_nn(const DevInst *d_inst, int count, cudaStream_t s)
+// shared memory sized for the largest instance, capped (each instance then
+// takes what fits, the rest stays in the workspace)
+static size_t ls_launch_smem(int max_n)
 {
-    k_two_opt_nn<<<count, 32, 0, s>>>(d_inst);
+    const size_t cap = 220 * 1024;
+    if (ls_smem_full(max_n) <= cap) return ls_smem_full(max_n);
+    return ls_smem_core(max_n) <= cap ? ls_smem_core(max_n) : 0;
 }
 
-void launch_two_opt_ib(const DevInst *d_inst, int count, cudaStream_t s)
+template <typename Kern>
+static void ls_launch(Kern kern, const DevInst *d_inst, int count, int max_n, cudaStream_t s)
 {
-    k_two_opt_ib<<<count, 32, 0, s>>>(d_inst);
+    const size_t smem = ls_launch_smem(max_n);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<count, 32, smem, s>>>(d_inst, (unsigned)smem);
+}
+
+void launch_two_opt_nn(const DevInst *d_inst, int count, int max_n, cudaStream_t s)
+{
+    ls_launch(k_two_opt_nn, d_inst, count, max_n, s);
+}
+
+void launch_two_opt_ib(const DevInst *d_inst, int count, int max_n, cudaStream_t s)
+{
+    ls_launch(k_two_opt_ib, d_inst, count, max_n, s);
 }
 
 }  // namespace hac

@@ -2,11 +2,7 @@
 // (Sec. III-D), one warp per instance, applied to T_NN once (Alg. 1 line 4)
 // and to the iteration-best tour before it updates the pheromone.
 //
-// The search is sequential by definition; the warp parallelises inside it:
-// the up-to-32 neighbour moves of a city are evaluated by one lane each and
-// the first improving one in list order is taken by ballot + ffs; don't-look
-// bits of 32 tour positions are tested per ballot; segment reversals swap
-// element pairs across lanes.  Order of the search:
+// Order of the search (it defines the result):
 //   rounds start with all bits clear; a round repeats passes over the tour
 //   positions until a pass makes no move; the search ends after a round whose
 //   first pass made no move (a local optimum of the neighbour-list moves).
@@ -20,6 +16,25 @@
 //   move of (pred a, pred b).  A call stops after 64n + 1024 moves (a bound
 //   that strictly decreasing tour lengths never reach in practice), so the
 //   kernel always terminates.
+//
+// Every move is decided in FP64 (d_ij as in the length, gain = (d(a,dir a) -
+// d(a,b)) + d(b,dir b) - d(dir a,dir b)).  FP32 copies only rule candidates
+// out: el[p] holds d(tour[p], tour[p+1]) in FP32 and nbrd32 the neighbour
+// distances.  Each FP32 distance is within 4 units of 2^-24 (relative) of the
+// FP64 one, so the FP32 estimate of the four-term gain is within about
+// 8 * 2^-24 of the sum of the four magnitudes; a candidate is examined in
+// FP64 unless its estimate lies below 1e-10 by more than 4e-6 times that sum
+// (plus 1e-18 for FP32 underflow).  Likewise d(a, b) is compared with
+// d(a, dir a) in FP32 with a relative margin of 4e-6 before the exact test.
+// The moves taken are therefore exactly those of the plain FP64 search.
+//
+// Parallelism inside the sequential search: a pass examines the next 32 tour
+// positions at once, one city per lane, with the FP32 test only; the cities
+// before the first one that might move have no move and get their bit at
+// once (as they would one by one, since examining a city without a move
+// changes nothing else), and that city is then examined by the whole warp, one
+// neighbour per lane, in FP64.  Segment reversals swap element pairs across
+// lanes.
 #pragma once
 
 #include "lengths.cuh"
@@ -27,94 +42,195 @@
 namespace hac {
 
 constexpr unsigned FULL2 = 0xffffffffu;
+constexpr float LS_G1_LO = 0.999996f;   // d(a,dir a) <= this * d(a,b) in FP32: g1 < 0 in FP64
 
 __device__ __forceinline__ int wrap_next(int p, int n) { return p + 1 < n ? p + 1 : 0; }
 __device__ __forceinline__ int wrap_prev(int p, int n) { return p > 0 ? p - 1 : n - 1; }
 
-// reverse so that (a, succ a), (b, succ b) become (a, b), (succ a, succ b)
-__device__ __forceinline__ void apply_succ_move(int32_t *tour, int32_t *pos, int n, int a, int b)
+// the arrays of one search: shared memory (a kernel of its own) or the workspace
+struct LsMem {
+    int32_t *tour;      // the tour being improved
+    int32_t *pos;       // pos[city]
+    uint8_t *dlb;       // don't-look bit by city
+    float *el;          // el[p] ~ d(tour[p], tour[p+1 mod n]), FP32
+    const float2 *xy;   // coordinates
+};
+
+__device__ __forceinline__ float ls_d32(const float2 *xy, int u, int v)
+{
+    const float2 p = xy[u], q = xy[v];
+    const float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y);
+    return __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
+}
+
+// false only if the FP64 gain is certainly <= LS_GAIN
+__device__ __forceinline__ bool ls_may_improve(float da, float dab, float dbb, float dn)
+{
+    const float est = __fsub_rn(__fadd_rn(__fsub_rn(da, dab), dbb), dn);
+    const float mag = __fadd_rn(__fadd_rn(da, dab), __fadd_rn(dbb, dn));
+    return est > __fsub_rn((float)LS_GAIN, __fadd_rn(__fmul_rn(4e-6f, mag), 1e-18f));
+}
+
+// reverse so that (x, succ x), (y, succ y) become (x, y), (succ x, succ y);
+// the inner edges of the reversed range swap, the two new edges get dxy, dss
+__device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, int y, float dxy, float dss)
 {
     const int lane = threadIdx.x & 31;
-    int i0 = wrap_next(pos[a], n);
-    int len = pos[b] - i0;
+    int i0 = wrap_next(M.pos[x], n);
+    int len = M.pos[y] - i0;
     if (len < 0) len += n;
     len += 1;
     if (2 * len > n) {
-        i0 = wrap_next(pos[b], n);
-        len = pos[a] - i0;
+        i0 = wrap_next(M.pos[y], n);
+        len = M.pos[x] - i0;
         if (len < 0) len += n;
         len += 1;
     }
     __syncwarp();
-    for (int x = lane; x < len / 2; x += 32) {
-        int p = i0 + x;
+    for (int t = lane; t < len / 2; t += 32) {
+        int p = i0 + t;
         if (p >= n) p -= n;
-        int q = i0 + len - 1 - x;
+        int q = i0 + len - 1 - t;
         if (q >= n) q -= n;
-        int u = tour[p], v = tour[q];
-        tour[p] = v;
-        tour[q] = u;
-        pos[v] = p;
-        pos[u] = q;
+        const int u = M.tour[p], v = M.tour[q];
+        M.tour[p] = v;
+        M.tour[q] = u;
+        M.pos[v] = p;
+        M.pos[u] = q;
+    }
+    for (int t = lane; t < (len - 1) / 2; t += 32) {
+        int p = i0 + t;
+        if (p >= n) p -= n;
+        int q = i0 + len - 2 - t;
+        if (q >= n) q -= n;
+        const float u = M.el[p], v = M.el[q];
+        M.el[p] = v;
+        M.el[q] = u;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        M.el[wrap_prev(i0, n)] = dxy;
+        int e = i0 + len - 1;
+        if (e >= n) e -= n;
+        M.el[e] = dss;
     }
     __syncwarp();
 }
 
-static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour)
+// FP32 test of one city by one lane: could some move of it improve?
+__device__ __forceinline__ bool ls_city_may_move(const DevInst &I, const LsMem &M, int n, int K, int a)
+{
+    const int32_t *nb = I.nbr + (size_t)a * K;
+    const float *nd = I.nbrd32 + (size_t)a * K;
+    const int pa = M.pos[a];
+    for (int dir = 0; dir < 2; ++dir) {
+        const int an = dir == 0 ? M.tour[wrap_next(pa, n)] : M.tour[wrap_prev(pa, n)];
+        const float da = M.el[dir == 0 ? pa : wrap_prev(pa, n)];
+        for (int k = 0; k < K; ++k) {
+            const float dab = nd[k];
+            if (!(da > __fmul_rn(dab, LS_G1_LO))) break;   // the list ascends: no later b either
+            const int b = nb[k];
+            const int pb = M.pos[b];
+            const int bn = dir == 0 ? M.tour[wrap_next(pb, n)] : M.tour[wrap_prev(pb, n)];
+            if (b == an || bn == a) continue;
+            const float dbb = M.el[dir == 0 ? pb : wrap_prev(pb, n)];
+            if (ls_may_improve(da, dab, dbb, ls_d32(M.xy, an, bn))) return true;
+        }
+    }
+    return false;
+}
+
+// One direction of city a, one neighbour per lane: the first improving move
+// in list order, decided in FP64.
+__device__ __forceinline__ bool ls_find_move(const DevInst &I, const LsMem &M, int n, int K, int a, int dir,
+                                             int nb, float nd32, double nd64, int &an, int &b, int &bn,
+                                             float &dab, float &dn)
+{
+    const int lane = threadIdx.x & 31;
+    const int pa = M.pos[a];
+    an = dir == 0 ? M.tour[wrap_next(pa, n)] : M.tour[wrap_prev(pa, n)];
+    const float da32 = M.el[dir == 0 ? pa : wrap_prev(pa, n)];
+    bool cand = false;
+    int bb = 0, bbn = 0;
+    if (lane < K && da32 > __fmul_rn(nd32, LS_G1_LO)) {
+        bb = nb;
+        const int pb = M.pos[bb];
+        bbn = dir == 0 ? M.tour[wrap_next(pb, n)] : M.tour[wrap_prev(pb, n)];
+        if (!(bb == an || bbn == a)) {
+            const float dbb = M.el[dir == 0 ? pb : wrap_prev(pb, n)];
+            cand = ls_may_improve(da32, nd32, dbb, ls_d32(M.xy, an, bbn));
+        }
+    }
+    if (!__ballot_sync(FULL2, cand)) return false;
+    const double da = dist64(I, a, an);
+    bool ok = false;
+    double dnn = 0.0;
+    if (cand) {
+        const double g1 = __dsub_rn(da, nd64);
+        if (g1 > 0.0) {
+            dnn = dist64(I, an, bbn);
+            const double gain = __dsub_rn(__dadd_rn(g1, dist64(I, bb, bbn)), dnn);
+            ok = gain > LS_GAIN;
+        }
+    }
+    const unsigned om = __ballot_sync(FULL2, ok);
+    if (!om) return false;
+    const int src = __ffs(om) - 1;
+    b = __shfl_sync(FULL2, bb, src);
+    bn = __shfl_sync(FULL2, bbn, src);
+    dab = __shfl_sync(FULL2, nd32, src);
+    dn = __double2float_rn(__shfl_sync(FULL2, dnn, src));
+    return true;
+}
+
+// Improves `tour` (global memory) in place.  M holds the working arrays; when
+// M.tour is not `tour`, the tour is copied in and back out.
+static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour, const LsMem &M)
 {
     const int lane = threadIdx.x & 31;
     const int n = I.n, K = I.ls_k;
-    int32_t *pos = I.ls_pos;
-    uint8_t *dlb = I.ls_dlb;
-    for (int p = lane; p < n; p += 32) pos[tour[p]] = p;
+    if (M.tour != tour)
+        for (int p = lane; p < n; p += 32) M.tour[p] = tour[p];
+    __syncwarp();
+    for (int p = lane; p < n; p += 32) M.pos[M.tour[p]] = p;
+    for (int p = lane; p < n; p += 32) M.el[p] = ls_d32(M.xy, M.tour[p], M.tour[wrap_next(p, n)]);
     __syncwarp();
     const long long max_moves = 64LL * n + 1024;
     long long moves = 0;
     int round_moves;
     do {
         round_moves = 0;
-        for (int p = lane; p < n; p += 32) dlb[p] = 0;
+        for (int p = lane; p < n; p += 32) M.dlb[p] = 0;
         __syncwarp();
         bool improved = true;
         while (improved && moves < max_moves) {
             improved = false;
             int p = 0;
             while (p < n && moves < max_moves) {
+                // the next 32 positions at once, FP32 test only
                 const int pp = p + lane;
-                const bool clear = pp < n && !dlb[tour[pp]];
-                const unsigned cm = __ballot_sync(FULL2, clear);
-                if (!cm) { p += 32; continue; }
-                p += __ffs(cm) - 1;
-                const int a = tour[p];
+                const int al = pp < n ? M.tour[pp] : 0;
+                const bool clear = pp < n && !M.dlb[al];
+                const bool flag = clear && ls_city_may_move(I, M, n, K, al);
+                const unsigned fm = __ballot_sync(FULL2, flag);
+                const int f = fm ? __ffs(fm) - 1 : 32;
+                if (clear && lane < f) M.dlb[al] = 1;   // examined, no move
+                __syncwarp();
+                if (!fm) { p += 32; continue; }
+                p += f;
+                const int a = M.tour[p];
+                const int nb = lane < K ? I.nbr[(size_t)a * K + lane] : 0;
+                const float nd32 = lane < K ? I.nbrd32[(size_t)a * K + lane] : 0.0f;
+                const double nd64 = lane < K ? I.nbrd[(size_t)a * K + lane] : 0.0;
                 for (;;) {
                     bool moved = false;
                     for (int dir = 0; dir < 2 && !moved; ++dir) {
-                        const int pa = pos[a];
-                        const int an = dir == 0 ? tour[wrap_next(pa, n)] : tour[wrap_prev(pa, n)];
-                        const double da = dist64(I, a, an);
-                        bool ok = false;
-                        int b = 0, bn = 0;
-                        if (lane < K) {
-                            b = I.nbr[(size_t)a * K + lane];
-                            const double g1 = __dsub_rn(da, I.nbrd[(size_t)a * K + lane]);
-                            if (g1 > 0.0) {
-                                const int pb = pos[b];
-                                bn = dir == 0 ? tour[wrap_next(pb, n)] : tour[wrap_prev(pb, n)];
-                                if (!(b == an || bn == a)) {
-                                    const double gain =
-                                        __dsub_rn(__dadd_rn(g1, dist64(I, b, bn)), dist64(I, an, bn));
-                                    ok = gain > LS_GAIN;
-                                }
-                            }
-                        }
-                        const unsigned om = __ballot_sync(FULL2, ok);
-                        if (om) {
-                            const int src = __ffs(om) - 1;
-                            b = __shfl_sync(FULL2, b, src);
-                            bn = __shfl_sync(FULL2, bn, src);
-                            if (dir == 0) apply_succ_move(tour, pos, n, a, b);
-                            else apply_succ_move(tour, pos, n, an, bn);
-                            if (lane == 0) { dlb[a] = 0; dlb[an] = 0; dlb[b] = 0; dlb[bn] = 0; }
+                        int an, b, bn;
+                        float dab, dn;
+                        if (ls_find_move(I, M, n, K, a, dir, nb, nd32, nd64, an, b, bn, dab, dn)) {
+                            if (dir == 0) apply_succ_move(M, n, a, b, dab, dn);
+                            else apply_succ_move(M, n, an, bn, dn, dab);
+                            if (lane == 0) { M.dlb[a] = 0; M.dlb[an] = 0; M.dlb[b] = 0; M.dlb[bn] = 0; }
                             __syncwarp();
                             moved = true;
                             improved = true;
@@ -124,12 +240,47 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
                     }
                     if (!moved || moves >= max_moves) break;
                 }
-                if (lane == 0) dlb[a] = 1;
+                if (lane == 0) M.dlb[a] = 1;
                 __syncwarp();
                 ++p;
             }
         }
     } while (round_moves > 0 && moves < max_moves);
+    if (M.tour != tour)
+        for (int p = lane; p < n; p += 32) tour[p] = M.tour[p];
+    __syncwarp();
+}
+
+// the workspace arrays of an instance (no shared memory)
+__device__ __forceinline__ LsMem ls_global(const DevInst &I, int32_t *tour)
+{
+    return LsMem{tour, I.ls_pos, I.ls_dlb, I.ls_el, reinterpret_cast<const float2 *>(I.xy)};
+}
+
+// shared memory: tour, pos, el (4n bytes each), dlb (n bytes), then the
+// coordinates at a 16-byte boundary when they fit as well
+__host__ __device__ inline size_t ls_smem_core(int n) { return (size_t)n * 13; }
+__host__ __device__ inline size_t ls_xy_offset(int n) { return ((size_t)n * 13 + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t ls_smem_full(int n) { return ls_xy_offset(n) + (size_t)n * 8; }
+
+// arrays in `sm` (smem_bytes) where they fit, else in the workspace; one warp
+__device__ __forceinline__ LsMem ls_shared(const DevInst &I, int32_t *tour, unsigned char *sm, size_t smem_bytes)
+{
+    const int n = I.n;
+    if (ls_smem_core(n) > smem_bytes) return ls_global(I, tour);
+    LsMem M;
+    M.tour = reinterpret_cast<int32_t *>(sm);
+    M.pos = reinterpret_cast<int32_t *>(sm + (size_t)n * 4);
+    M.el = reinterpret_cast<float *>(sm + (size_t)n * 8);
+    M.dlb = sm + (size_t)n * 12;
+    M.xy = reinterpret_cast<const float2 *>(I.xy);
+    if (ls_smem_full(n) <= smem_bytes) {
+        float2 *sxy = reinterpret_cast<float2 *>(sm + ls_xy_offset(n));
+        for (int p = threadIdx.x & 31; p < n; p += 32) sxy[p] = reinterpret_cast<const float2 *>(I.xy)[p];
+        __syncwarp();
+        M.xy = sxy;
+    }
+    return M;
 }
 
 }  // namespace hac

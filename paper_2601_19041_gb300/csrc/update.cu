@@ -40,13 +40,13 @@ __global__ void k_update(const DevInst *insts, const int2 *slotmap)
     I.choice[s] = update_slot(I, s, (int)(s / I.k_pad), j, omega, delta, st->tau_min, st->tau_max);
 }
 
-void launch_two_opt_ib(const DevInst *d_inst, int count, cudaStream_t s);
+void launch_two_opt_ib(const DevInst *d_inst, int count, int max_n, cudaStream_t s);
 
 int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
-                          int slotmap_len, bool any_ls, cudaStream_t s)
+                          int slotmap_len, bool any_ls, int max_n, cudaStream_t s)
 {
     k_select<<<count, 256, 0, s>>>(d_inst);
-    if (any_ls) launch_two_opt_ib(d_inst, count, s);
+    if (any_ls) launch_two_opt_ib(d_inst, count, max_n, s);
     k_gb<<<count, 256, 0, s>>>(d_inst);
     k_update<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
     return any_ls ? 4 : 3;
