@@ -28,13 +28,15 @@
 // d(a, dir a) in FP32 with a relative margin of 4e-6 before the exact test.
 // The moves taken are therefore exactly those of the plain FP64 search.
 //
-// Parallelism inside the sequential search: a pass examines the next 32 tour
-// positions at once, one city per lane, with the FP32 test only; the cities
-// before the first one that might move have no move and get their bit at
-// once (as they would one by one, since examining a city without a move
-// changes nothing else), and that city is then examined by the whole warp, one
-// neighbour per lane, in FP64.  Segment reversals swap element pairs across
-// lanes.
+// Parallelism inside the sequential search: when more than LS_FEW of the
+// next 32 tour positions hold cities whose bit is clear, a pass examines them
+// at once, one city per lane, with the FP32 test only; the cities before the
+// first one that might move have no move and get their bit at once (as they
+// would one by one, since examining a city without a move changes nothing
+// else).  A city that might move, or the first clear one when few are clear,
+// is examined by the whole warp, one neighbour per lane (FP32 test, then FP64
+// for the candidates that pass it).  Segment reversals swap element pairs
+// across lanes.
 #pragma once
 
 #include "lengths.cuh"
@@ -43,6 +45,7 @@ namespace hac {
 
 constexpr unsigned FULL2 = 0xffffffffu;
 constexpr float LS_G1_LO = 0.999996f;   // d(a,dir a) <= this * d(a,b) in FP32: g1 < 0 in FP64
+constexpr int LS_FEW = 4;               // at most this many clear cities in 32 positions: one at a time
 
 __device__ __forceinline__ int wrap_next(int p, int n) { return p + 1 < n ? p + 1 : 0; }
 __device__ __forceinline__ int wrap_prev(int p, int n) { return p > 0 ? p - 1 : n - 1; }
@@ -126,16 +129,27 @@ __device__ __forceinline__ bool ls_city_may_move(const DevInst &I, const LsMem &
     for (int dir = 0; dir < 2; ++dir) {
         const int an = dir == 0 ? M.tour[wrap_next(pa, n)] : M.tour[wrap_prev(pa, n)];
         const float da = M.el[dir == 0 ? pa : wrap_prev(pa, n)];
-        for (int k = 0; k < K; ++k) {
-            const float dab = nd[k];
-            if (!(da > __fmul_rn(dab, LS_G1_LO))) break;   // the list ascends: no later b either
-            const int b = nb[k];
-            const int pb = M.pos[b];
-            const int bn = dir == 0 ? M.tour[wrap_next(pb, n)] : M.tour[wrap_prev(pb, n)];
-            if (b == an || bn == a) continue;
-            const float dbb = M.el[dir == 0 ? pb : wrap_prev(pb, n)];
-            if (ls_may_improve(da, dab, dbb, ls_d32(M.xy, an, bn))) return true;
+        for (int k0 = 0; k0 < K; k0 += 4) {
+            // four neighbours' entries at once (independent loads), then in order
+            float dab4[4];
+            int b4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dab4[q] = k0 + q < K ? nd[k0 + q] : __int_as_float(0x7f800000);
+                b4[q] = k0 + q < K ? nb[k0 + q] : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!(da > __fmul_rn(dab4[q], LS_G1_LO))) goto next_dir;   // the list ascends: no later b either
+                const int b = b4[q];
+                const int pb = M.pos[b];
+                const int bn = dir == 0 ? M.tour[wrap_next(pb, n)] : M.tour[wrap_prev(pb, n)];
+                if (b == an || bn == a) continue;
+                const float dbb = M.el[dir == 0 ? pb : wrap_prev(pb, n)];
+                if (ls_may_improve(da, dab4[q], dbb, ls_d32(M.xy, an, bn))) return true;
+            }
         }
+    next_dir:;
     }
     return false;
 }
@@ -207,17 +221,23 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
             improved = false;
             int p = 0;
             while (p < n && moves < max_moves) {
-                // the next 32 positions at once, FP32 test only
                 const int pp = p + lane;
                 const int al = pp < n ? M.tour[pp] : 0;
                 const bool clear = pp < n && !M.dlb[al];
-                const bool flag = clear && ls_city_may_move(I, M, n, K, al);
-                const unsigned fm = __ballot_sync(FULL2, flag);
-                const int f = fm ? __ffs(fm) - 1 : 32;
-                if (clear && lane < f) M.dlb[al] = 1;   // examined, no move
-                __syncwarp();
-                if (!fm) { p += 32; continue; }
-                p += f;
+                const unsigned cm = __ballot_sync(FULL2, clear);
+                if (!cm) { p += 32; continue; }
+                if (__popc(cm) <= LS_FEW) {
+                    p += __ffs(cm) - 1;     // few clear cities: the warp examines the first one
+                } else {
+                    // many: the next 32 positions at once, one city per lane, FP32 test only
+                    const bool flag = clear && ls_city_may_move(I, M, n, K, al);
+                    const unsigned fm = __ballot_sync(FULL2, flag);
+                    const int f = fm ? __ffs(fm) - 1 : 32;
+                    if (clear && lane < f) M.dlb[al] = 1;   // examined, no move
+                    __syncwarp();
+                    if (!fm) { p += 32; continue; }
+                    p += f;
+                }
                 const int a = M.tour[p];
                 const int nb = lane < K ? I.nbr[(size_t)a * K + lane] : 0;
                 const float nd32 = lane < K ? I.nbrd32[(size_t)a * K + lane] : 0.0f;
