@@ -21,6 +21,9 @@
  *   decode             brute-force optima (n <= 9), closed-form optima (circle,
  *                      grid) under a heatmap concentrated on the optimal tour
  *   2-opt              no improving neighbour-list move remains; never lengthens
+ *   MMAS schedule      u_gb tightens from 25 to 1 (Sec. III-B); branching factor
+ *                      on pheromone matrices of known form (all equal: k_eff/d*;
+ *                      converged: 1); restarts only at checks, T_gb kept
  */
 #include <math.h>
 #include <stdint.h>
@@ -49,6 +52,7 @@ typedef struct {
     int32_t local_search;    /* 0 none, 1 2-opt on the iteration-best tour */
     int32_t baseline_scope;  /* 0 order statistic over C_i, 1 over the whole heatmap row */
     int32_t ls_k;            /* geometric neighbour-list size of the 2-opt */
+    int32_t schedule;        /* 0: T+ = T_ib always; 1: MMAS u_gb schedule and restarts */
     uint64_t seed;
 } orc_params;
 
@@ -282,9 +286,17 @@ typedef struct {
     double *lens;       /* m */
     int32_t *ib_tour;   /* n, last iteration-best (after local search) */
     double L_ib;
+    /* MMAS schedule (schedule = 1) */
+    int32_t *rb_tour;   /* restart-best tour */
+    double L_rb;        /* +inf while cleared */
+    int32_t t_restart;  /* iteration of the last restart (0: none) */
+    int32_t t_rbimp;    /* iteration of the last restart-best improvement */
+    int32_t u_gb;       /* period of the T_rb deposit for the next iteration */
+    int32_t n_restarts;
     int32_t cap;        /* trace capacity */
     int32_t *tr_ib;     /* per iteration: iteration-best ant */
-    double *tr_Lib, *tr_Lgb;
+    double *tr_Lib, *tr_Lgb, *tr_Lrb;
+    int32_t *tr_code;   /* per iteration: 1 = T_rb deposited, 2 = restart (or both) */
     int64_t n_fallback; /* construction steps that took the nearest-unvisited rule */
     uint8_t *visited;
 } orc_state;
@@ -674,6 +686,52 @@ static void construct(orc_state *S, int a, int32_t *T, double *Lout)
     *Lout = orc_tour_length(in, T);
 }
 
+/* --------------------------------------------- MMAS schedule (Alg. 1, III-B)
+ *
+ * Sec. III-B keeps the MMAS machinery: the elite tour T+ is the iteration-best
+ * tour on most iterations and the restart-best tour every u_gb iterations,
+ * u_gb tightening from 25 to 1 as the search goes on; every 100 iterations,
+ * when the restart-best tour has not improved for more than 250 iterations and
+ * the branching factor is below lambda_bf = 1 + 1e-5 (band fraction
+ * xi_bf = 0.05, Sec. IV-D), the pheromone is reset to tau_max and the
+ * restart-best tour is cleared; the global-best tour is kept.  The steps of
+ * u_gb and the branching-factor normalisation are not printed in the paper;
+ * the ones used here are the MMAS ones (Stuetzle and Hoos, 2000): u_gb = 25,
+ * 5, 3, 2, 1 for s < 25, 75, 125, 250 and beyond, s = iterations since the
+ * last restart (or the start), and the mean per-node count of candidate
+ * slots with tau >= min_i + xi_bf (max_i - min_i), divided by d*.
+ */
+
+int orc_ugb(int32_t s)
+{
+    if (s < 25) return 25;
+    if (s < 75) return 5;
+    if (s < 125) return 3;
+    if (s < 250) return 2;
+    return 1;
+}
+
+double orc_branching(const float *tau, const int32_t *cand, int n, int kp, int dstar)
+{
+    int64_t count = 0;
+    for (int i = 0; i < n; ++i) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int c = 0; c < kp; ++c) {
+            int64_t s = (int64_t)i * kp + c;
+            if (cand[s] < 0) continue;
+            double v = (double)tau[s];
+            if (v < lo) lo = v;
+            if (v > hi) hi = v;
+        }
+        double cut = lo + 0.05 * (hi - lo);
+        for (int c = 0; c < kp; ++c) {
+            int64_t s = (int64_t)i * kp + c;
+            if (cand[s] >= 0 && (double)tau[s] >= cut) ++count;
+        }
+    }
+    return (double)count / ((double)n * (double)dstar);
+}
+
 /* ------------------------------------------------- one iteration (Alg. 1) */
 
 static void iterate_once(orc_state *S)
@@ -688,21 +746,35 @@ static void iterate_once(orc_state *S)
         orc_two_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
         S->L_ib = orc_tour_length(&S->in, S->ib_tour);
     }
+    const int32_t t1 = S->t + 1;                         /* this iteration, counted from 1 */
+    int use_rb = 0, code = 0;
+    if (S->p.schedule) {                                 /* restart-best, then the elite choice */
+        if (S->L_ib < S->L_rb) {
+            memcpy(S->rb_tour, S->ib_tour, (size_t)n * sizeof(int32_t));
+            S->L_rb = S->L_ib;
+            S->t_rbimp = t1;
+        }
+        use_rb = t1 % S->u_gb == 0;
+        code = use_rb;
+    }
     if (S->L_ib < S->L_gb) {                             /* new global best: recompute bounds */
         memcpy(S->gb_tour, S->ib_tour, (size_t)n * sizeof(int32_t));
         S->L_gb = S->L_ib;
         set_bounds(S, S->L_gb);
     }
-    /* Evaporate and deposit on T+ = T_ib, eqs. (pheromone_update)/(pheromone_delta),
-     * on the stored candidate edges only.  A symmetric instance deposits on the
-     * slot of either orientation of a tour edge; an ATSP only on i -> succ(i). */
+    /* Evaporate and deposit on T+ (T_ib, or T_rb by the schedule), eqs.
+     * (pheromone_update)/(pheromone_delta), on the stored candidate edges only.
+     * A symmetric instance deposits on the slot of either orientation of a
+     * tour edge; an ATSP only on i -> succ(i). */
+    const int32_t *elite = use_rb ? S->rb_tour : S->ib_tour;
+    const double L_elite = use_rb ? S->L_rb : S->L_ib;
     int32_t *succ = xcalloc((size_t)n, sizeof *succ), *pred = xcalloc((size_t)n, sizeof *pred);
     for (int s = 0; s < n; ++s) {
-        int u = S->ib_tour[s], v = S->ib_tour[(s + 1) % n];
+        int u = elite[s], v = elite[(s + 1) % n];
         succ[u] = v; pred[v] = u;
     }
     float omega = (float)(1.0 - S->p.rho);
-    float delta = (float)(1.0 / S->L_ib);
+    float delta = (float)(1.0 / L_elite);
     int sym = S->in.kind == 0;
     for (int i = 0; i < n; ++i)
         for (int c = 0; c < kp; ++c) {
@@ -716,8 +788,25 @@ static void iterate_once(orc_state *S)
             S->choice[s] = choice_of(S, S->tau[s], S->W[s]);
         }
     free(succ); free(pred);
+    if (S->p.schedule) {                                 /* restart check, then the next u_gb */
+        if (t1 % 100 == 0 && t1 - S->t_rbimp > 250 &&
+            orc_branching(S->tau, S->cand, n, kp, S->p.degree_target) < 1.0 + 1e-5) {
+            for (int64_t s = 0; s < (int64_t)n * kp; ++s)
+                if (S->cand[s] >= 0) {
+                    S->tau[s] = S->tau_max;
+                    S->choice[s] = choice_of(S, S->tau[s], S->W[s]);
+                }
+            S->L_rb = INFINITY;
+            S->t_restart = t1;
+            S->t_rbimp = t1;
+            S->n_restarts++;
+            code |= 2;
+        }
+        S->u_gb = orc_ugb(t1 - S->t_restart);
+    }
     if (S->t < S->cap) {
         S->tr_ib[S->t] = ib; S->tr_Lib[S->t] = S->L_ib; S->tr_Lgb[S->t] = S->L_gb;
+        S->tr_Lrb[S->t] = S->L_rb; S->tr_code[S->t] = code;
     }
     S->t++;
 }
@@ -742,6 +831,7 @@ static int check_inputs(const orc_instance *in, const orc_params *p)
         }
     }
     if (p->rho <= 0.0 || p->rho >= 1.0 || p->degree_target < 1) return ORC_EINVAL;
+    if (p->schedule != 0 && p->schedule != 1) return ORC_EINVAL;
     if (p->local_search && (in->kind != 0 || p->ls_k < 1 || p->ls_k > in->n - 1)) return ORC_EINVAL;
     return ORC_OK;
 }
@@ -754,6 +844,7 @@ void orc_destroy(void *h)
     free(S->logev); free(S->W); free(S->nbr); free(S->nn_tour); free(S->tau);
     free(S->choice); free(S->gb_tour); free(S->tours); free(S->lens); free(S->ib_tour);
     free(S->tr_ib); free(S->tr_Lib); free(S->tr_Lgb); free(S->visited);
+    free(S->rb_tour); free(S->tr_Lrb); free(S->tr_code);
     free(S);
 }
 
@@ -783,9 +874,13 @@ void *orc_create(const orc_instance *in, const orc_params *p, int32_t *status)
     S->tr_ib = xcalloc((size_t)S->cap, sizeof *S->tr_ib);
     S->tr_Lib = xcalloc((size_t)S->cap, sizeof *S->tr_Lib);
     S->tr_Lgb = xcalloc((size_t)S->cap, sizeof *S->tr_Lgb);
+    S->tr_Lrb = xcalloc((size_t)S->cap, sizeof *S->tr_Lrb);
+    S->tr_code = xcalloc((size_t)S->cap, sizeof *S->tr_code);
+    S->rb_tour = xcalloc(n, sizeof *S->rb_tour);
     if (!S->cand || !S->cdist || !S->conf || !S->base || !S->evid || !S->logev || !S->W ||
         !S->nbr || !S->nn_tour || !S->tau || !S->choice || !S->gb_tour || !S->tours ||
-        !S->lens || !S->ib_tour || !S->visited || !S->tr_ib || !S->tr_Lib || !S->tr_Lgb) {
+        !S->lens || !S->ib_tour || !S->visited || !S->tr_ib || !S->tr_Lib || !S->tr_Lgb ||
+        !S->tr_Lrb || !S->tr_code || !S->rb_tour) {
         orc_destroy(S);
         if (status) *status = ORC_ENOMEM;
         return NULL;
@@ -803,6 +898,8 @@ void *orc_create(const orc_instance *in, const orc_params *p, int32_t *status)
     }
     memcpy(S->gb_tour, S->nn_tour, n * sizeof(int32_t));   /* line 6 */
     S->L_gb = S->L_nn;
+    S->L_rb = INFINITY;                   /* restart-best: none yet */
+    S->u_gb = 25;
     return S;
 }
 
@@ -820,7 +917,7 @@ enum {
     ORC_F_CAND = 1, ORC_F_CDIST, ORC_F_CONF, ORC_F_BASE, ORC_F_EVID, ORC_F_LOGEV, ORC_F_W,
     ORC_F_TAU, ORC_F_CHOICE, ORC_F_NN_TOUR, ORC_F_GB_TOUR, ORC_F_TOURS, ORC_F_LENS,
     ORC_F_IB_TOUR, ORC_F_TRACE_IB, ORC_F_TRACE_LIB, ORC_F_TRACE_LGB, ORC_F_NBR,
-    ORC_F_SCALARS, ORC_F_INTS
+    ORC_F_SCALARS, ORC_F_INTS, ORC_F_RB_TOUR, ORC_F_TRACE_LRB, ORC_F_TRACE_CODE
 };
 
 int orc_get(void *h, int32_t field, void *dst, int64_t bytes)
@@ -830,8 +927,8 @@ int orc_get(void *h, int32_t field, void *dst, int64_t bytes)
     size_t n = (size_t)S->n, slots = n * (size_t)S->k_pad, m = (size_t)S->p.m;
     const void *src = NULL;
     size_t sz = 0;
-    double scal[12];
-    int64_t ints[6];
+    double scal[13];
+    int64_t ints[10];
     switch (field) {
     case ORC_F_CAND: src = S->cand; sz = slots * 4; break;
     case ORC_F_CDIST: src = S->cdist; sz = slots * 8; break;
@@ -851,15 +948,19 @@ int orc_get(void *h, int32_t field, void *dst, int64_t bytes)
     case ORC_F_TRACE_LIB: src = S->tr_Lib; sz = (size_t)S->cap * 8; break;
     case ORC_F_TRACE_LGB: src = S->tr_Lgb; sz = (size_t)S->cap * 8; break;
     case ORC_F_NBR: src = S->nbr; sz = n * (size_t)(S->ls_k ? S->ls_k : 1) * 4; break;
+    case ORC_F_RB_TOUR: src = S->rb_tour; sz = n * 4; break;
+    case ORC_F_TRACE_LRB: src = S->tr_Lrb; sz = (size_t)S->cap * 8; break;
+    case ORC_F_TRACE_CODE: src = S->tr_code; sz = (size_t)S->cap * 4; break;
     case ORC_F_SCALARS:
         scal[0] = S->q90; scal[1] = S->Rhat; scal[2] = S->kappa; scal[3] = S->p_x;
         scal[4] = S->L_nn; scal[5] = S->tau_max64; scal[6] = S->tau_min64;
         scal[7] = (double)S->tau_max; scal[8] = (double)S->tau_min; scal[9] = S->L_gb;
-        scal[10] = S->L_ib; scal[11] = (double)S->n_lambda;
+        scal[10] = S->L_ib; scal[11] = (double)S->n_lambda; scal[12] = S->L_rb;
         src = scal; sz = sizeof scal; break;
     case ORC_F_INTS:
         ints[0] = S->n; ints[1] = S->k_eff; ints[2] = S->k_pad; ints[3] = S->t;
-        ints[4] = S->n_fallback; ints[5] = S->ls_k;
+        ints[4] = S->n_fallback; ints[5] = S->ls_k; ints[6] = S->n_restarts; ints[7] = S->t_restart;
+        ints[8] = S->t_rbimp; ints[9] = S->u_gb;
         src = ints; sz = sizeof ints; break;
     default: return ORC_EINVAL;
     }

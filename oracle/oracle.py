@@ -46,12 +46,14 @@ class _Params(C.Structure):
                 ("theta_h", C.c_double), ("eps", C.c_double), ("c_cap", C.c_double),
                 ("q_level", C.c_double), ("p_best", C.c_double), ("logw_clip", C.c_double),
                 ("degree_target", C.c_int32), ("local_search", C.c_int32),
-                ("baseline_scope", C.c_int32), ("ls_k", C.c_int32), ("seed", C.c_uint64)]
+                ("baseline_scope", C.c_int32), ("ls_k", C.c_int32), ("schedule", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 F = dict(cand=1, cdist=2, conf=3, base=4, evid=5, logev=6, W=7, tau=8, choice=9,
          nn_tour=10, gb_tour=11, tours=12, lens=13, ib_tour=14, trace_ib=15,
-         trace_Lib=16, trace_Lgb=17, nbr=18, scalars=19, ints=20)
+         trace_Lib=16, trace_Lgb=17, nbr=18, scalars=19, ints=20, rb_tour=21, trace_Lrb=22,
+         trace_code=23)
 
 _lib = None
 
@@ -79,6 +81,9 @@ def lib():
         L.orc_dist.argtypes = [C.POINTER(_Inst), C.c_int, C.c_int]; L.orc_dist.restype = C.c_double
         L.orc_key.argtypes = [C.POINTER(_Inst), C.c_int, C.c_int]; L.orc_key.restype = C.c_float
         L.orc_heat.argtypes = [C.POINTER(_Inst), C.c_int, C.c_int]; L.orc_heat.restype = C.c_double
+        L.orc_ugb.argtypes = [C.c_int32]; L.orc_ugb.restype = C.c_int
+        L.orc_branching.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int]
+        L.orc_branching.restype = C.c_double
         _lib = L
     return _lib
 
@@ -107,7 +112,7 @@ class _InstHolder:
 def _params(p) -> _Params:
     return _Params(p.m, p.k, p.iterations, p.alpha, p.beta, p.rho, p.theta_h, p.eps, p.c_cap,
                    p.q_level, p.p_best, p.logw_clip, p.degree_target, p.local_search,
-                   p.baseline_scope, p.ls_k, p.seed)
+                   p.baseline_scope, p.ls_k, getattr(p, "schedule", 0), p.seed)
 
 
 class Oracle:
@@ -120,7 +125,7 @@ class Oracle:
         self.h = lib().orc_create(C.byref(self._inst.s), C.byref(self._p), C.byref(st))
         if not self.h:
             raise ValueError(f"oracle rejected the instance (status {st.value})")
-        ints = self._get_raw("ints", np.int64, 6)
+        ints = self._get_raw("ints", np.int64, 10)
         self.n, self.k_eff, self.k_pad = int(ints[0]), int(ints[1]), int(ints[2])
         self.m = params.m
         self.ls_k = int(ints[5])
@@ -156,19 +161,23 @@ class Oracle:
                       trace_ib=(np.int32, (max(self.iterations, 1),)),
                       trace_Lib=(np.float64, (max(self.iterations, 1),)),
                       trace_Lgb=(np.float64, (max(self.iterations, 1),)),
+                      trace_Lrb=(np.float64, (max(self.iterations, 1),)),
+                      trace_code=(np.int32, (max(self.iterations, 1),)),
+                      rb_tour=(np.int32, (n,)),
                       nbr=(np.int32, (n, max(self.ls_k, 1))))
         dt, shp = shapes[field]
         return self._get_raw(field, dt, int(np.prod(shp))).reshape(shp)
 
     def scalars(self) -> dict:
-        s = self._get_raw("scalars", np.float64, 12)
+        s = self._get_raw("scalars", np.float64, 13)
         keys = ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
-                "tau_min", "L_gb", "L_ib", "n_lambda")
+                "tau_min", "L_gb", "L_ib", "n_lambda", "L_rb")
         return dict(zip(keys, s.tolist()))
 
     def ints(self) -> dict:
-        v = self._get_raw("ints", np.int64, 6)
-        return dict(zip(("n", "k_eff", "k_pad", "t", "n_fallback", "ls_k"), v.tolist()))
+        v = self._get_raw("ints", np.int64, 10)
+        return dict(zip(("n", "k_eff", "k_pad", "t", "n_fallback", "ls_k", "n_restarts", "t_restart",
+                         "t_rbimp", "u_gb"), v.tolist()))
 
 
 def solve(inst, params):
@@ -231,3 +240,14 @@ def dist(inst, i, j):
 def heat(inst, i, j):
     h = _InstHolder(inst)
     return lib().orc_heat(C.byref(h.s), i, j)
+
+
+def ugb(s):
+    return int(lib().orc_ugb(int(s)))
+
+
+def branching(tau, cand, dstar):
+    tau = np.ascontiguousarray(tau, np.float32)
+    cand = np.ascontiguousarray(cand, np.int32)
+    n, kp = tau.shape
+    return lib().orc_branching(tau.ctypes.data, cand.ctypes.data, n, kp, int(dstar))

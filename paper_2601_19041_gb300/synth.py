@@ -68,6 +68,7 @@ class Params:
     baseline_scope: int = 0
     ls_k: int = 20
     seed: int = 0
+    schedule: int = 0                 # 1: MMAS u_gb schedule and restarts (Sec. III-B)
 
 
 # ----------------------------------------------------------------------------- points
