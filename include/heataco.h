@@ -88,6 +88,15 @@ typedef struct {
  *                   iteration-best tour and on T_NN; tau_min = tau_max/(2n).
  *   baseline_scope  0: order statistic b_i over the candidates C_i; 1: over all
  *                   heatmap entries of row i (eq. background).
+ *   schedule        0 (default): T+ = the iteration-best tour every iteration;
+ *                   1: the MMAS machinery of Sec. III-B and Algorithm 1 --
+ *                   restart-best tour T_rb, elite T+ = T_rb every u_gb
+ *                   iterations (u_gb = 25, 5, 3, 2, 1 after 0, 25, 75, 125,
+ *                   250 iterations since the last restart), and every 100
+ *                   iterations a restart (tau <- tau_max, T_rb cleared, T_gb
+ *                   kept) when T_rb has not improved for more than 250
+ *                   iterations and the branching factor (band 0.05, per node,
+ *                   divided by d*) is below 1 + 1e-5.
  *   seed            key of the instance's Philox stream. */
 typedef struct {
     int32_t m, k, iterations;
@@ -97,6 +106,7 @@ typedef struct {
     int32_t local_search;
     int32_t baseline_scope;
     int32_t ls_k;
+    int32_t schedule;
     uint64_t seed;
 } hac_params;
 
@@ -170,11 +180,12 @@ int hac_batch_sync(hac_batch *bt);
  *   IB_TOUR int32 n         last iteration-best tour (after local search)
  *   TOURS  int32  m*n       the m tours of the last iteration
  *   LENS   f64    m         their lengths
- *   SCALARS f64   16        q90, Rhat, kappa, p_x, L_nn, tau_max64, tau_min64,
+ *   SCALARS f64   20        q90, Rhat, kappa, p_x, L_nn, tau_max64, tau_min64,
  *                           tau_max, tau_min, L_gb, L_ib, n_lambda, t, ib_ant,
- *                           n_fallback, k_pad
+ *                           n_fallback, k_pad, L_rb, n_restarts, t_restart, u_gb
  *   NBR    int32  n*ls_k    geometric 2-opt neighbour lists
- *   TRACE  f64    3*I       per iteration: ib ant, L_ib, L_gb
+ *   TRACE  f64    5*I       per iteration: ib ant, L_ib, L_gb, L_rb (+inf when
+ *                           cleared), code (1: T_rb deposited, 2: restart)
  * The call synchronises the stream. */
 enum hac_field {
     HAC_F_CAND = 1, HAC_F_CDIST, HAC_F_CONF, HAC_F_BASE, HAC_F_EVID, HAC_F_W, HAC_F_TAU,

@@ -420,7 +420,7 @@ int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size
         src = D.nbr; sz = n * D.ls_k * 4; break;
     case HAC_F_TRACE: src = D.trace; sz = (size_t)TRACE_W * std::max(D.iters, 1) * 8; break;
     case HAC_F_SCALARS: {
-        if (bytes < 16 * sizeof(double)) return HAC_EINVAL;
+        if (bytes < 20 * sizeof(double)) return HAC_EINVAL;
         InstState S0;
         CK(cudaMemcpy(&S0, D.st, sizeof S0, cudaMemcpyDeviceToHost));
         double *o = (double *)host_dst;
@@ -428,6 +428,7 @@ int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size
         o[5] = S0.tau_max64; o[6] = S0.tau_min64; o[7] = S0.tau_max; o[8] = S0.tau_min;
         o[9] = S0.L_gb; o[10] = S0.L_ib; o[11] = S0.n_lambda; o[12] = S0.t; o[13] = S0.ib;
         o[14] = (double)S0.n_fallback; o[15] = D.k_pad;
+        o[16] = S0.L_rb; o[17] = S0.n_restarts; o[18] = S0.t_restart; o[19] = S0.u_gb;
         return HAC_OK;
     }
     default: return HAC_EINVAL;

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
             __threadfence();
         }
         cl.sync();
-        const float delta = __double2float_rn(__ddiv_rn(1.0, st->L_ib));
+        const float delta = __double2float_rn(__ddiv_rn(1.0, st->L_dep));
         const float tmin = st->tau_min, tmax = st->tau_max;
         for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
             const int j = sidx[e];
@@ -149,6 +149,35 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
             const int l = e / kp, c = e - l * kp;
             const int i = rank + (l << CLOG);
             sch[e] = update_slot(I, (size_t)i * kp + c, i, j, omega, delta, tmin, tmax);
+        }
+        if (I.schedule) {   // restart check over every CTA's rows, then the next u_gb
+            __threadfence();
+            cl.sync();
+            if (schedule_check_due(I, st)) {
+                unsigned long long cnt = 0;
+                for (int l = threadIdx.x; l < R; l += blockDim.x) {
+                    const int i = rank + (l << CLOG);
+                    if (i < n) cnt += (unsigned long long)row_branching(I, i);
+                }
+                if (cnt) atomicAdd(&st->bf_count, cnt);
+                __threadfence();
+                cl.sync();
+                if (schedule_restart(I, st->bf_count)) {
+                    for (int e = threadIdx.x; e < R * kp; e += blockDim.x) {
+                        if ((int)sidx[e] >= n) continue;
+                        const int l = e / kp, c = e - l * kp;
+                        const size_t s = (size_t)(rank + (l << CLOG)) * kp + c;
+                        I.tau[s] = tmax;
+                        sch[e] = choice_value(I, tmax, I.W[s]);
+                    }
+                    if (rank == 0 && threadIdx.x == 0) schedule_finish(I, st, true);
+                } else if (rank == 0 && threadIdx.x == 0) {
+                    schedule_finish(I, st, false);
+                }
+            } else if (rank == 0 && threadIdx.x == 0) {
+                schedule_finish(I, st, false);
+            }
+            __threadfence();
         }
         cl.sync();
     }

@@ -17,7 +17,7 @@ namespace hac {
 constexpr int KMAX = HAC_KMAX;
 constexpr double DFLOOR = 1e-9;     // eta = 1/max(d, 1e-9): coincident points
 constexpr double LS_GAIN = 1e-10;   // 2-opt moves need a gain above this
-constexpr int TRACE_W = 3;          // trace entries per iteration: ib ant, L_ib, L_gb
+constexpr int TRACE_W = 5;          // trace entries per iteration: ib ant, L_ib, L_gb, L_rb, code
 
 // Per-instance scalars that live on the device (read back through HAC_F_SCALARS).
 struct InstState {
@@ -29,12 +29,20 @@ struct InstState {
     int32_t n_lambda;
     unsigned long long n_fallback;
     int32_t fbl_unsafe; // 1: some choice value could reach 0, lookup lists keep the candidates
+    // MMAS schedule (schedule = 1)
+    double L_rb;        // restart-best length, +inf while cleared
+    double L_dep;       // length of the tour T+ that deposits this iteration
+    int32_t t_restart;  // iteration of the last restart (0: none)
+    int32_t t_rbimp;    // iteration of the last restart-best improvement
+    int32_t u_gb;       // T_rb deposits when the iteration is a multiple of this
+    int32_t n_restarts;
+    unsigned long long bf_count;   // branching-factor count of the current check
 };
 
 // Device view of one instance: sizes, parameters and pointers into the workspace.
 struct DevInst {
     int32_t n, kind, k, k_eff, k_pad, m, iters, ls_k;
-    int32_t degree_target, local_search, baseline_scope, symmetrize, h_half;
+    int32_t degree_target, local_search, baseline_scope, symmetrize, h_half, schedule;
     uint64_t seed;
     double alpha, beta, rho, theta_h, eps, c_cap, q_level, p_best, logw_clip;
     // inputs
@@ -65,6 +73,7 @@ struct DevInst {
     int32_t fbl_len;
     // search state
     int32_t *nn_tour, *gb_tour, *ib_tour, *succ, *pred;   // n each
+    int32_t *rb_tour;         // n, restart-best tour (schedule = 1)
     int32_t *tours;           // m*n: tour of ant a, step s at a*tour_sa + s*tour_ss
     int32_t tour_sa, tour_ss; // (n, 1) ant-major, or (1, m) step-major (one ant per lane)
     uint8_t *slots;           // m*n chosen slot per step (same layout as tours), 0xff: nearest-unvisited

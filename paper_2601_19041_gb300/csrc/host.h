@@ -60,6 +60,7 @@ inline int check_params(const hac_instance &in, const hac_params &p)
     if (!(p.q_level >= 0.0 && p.q_level <= 1.0) || !(p.p_best > 0.0 && p.p_best < 1.0)) return HAC_EINVAL;
     if (!(p.c_cap >= 0.0) || !(p.logw_clip > 0.0)) return HAC_EINVAL;
     if (p.baseline_scope != 0 && p.baseline_scope != 1) return HAC_EINVAL;
+    if (p.schedule != 0 && p.schedule != 1) return HAC_EINVAL;
     if (p.local_search != 0 && p.local_search != 1) return HAC_EINVAL;
     if (p.local_search) {
         if (in.kind != 0) return HAC_EUNSUPPORTED;
@@ -164,6 +165,7 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
     put("fbl", A.take(n * FBL_LEN * 4));
     put("nn_tour", A.take(n * 4));
     put("gb_tour", A.take(n * 4));
+    put("rb_tour", A.take(n * 4));
     put("ib_tour", A.take(n * 4));
     put("succ", A.take(n * 4));
     put("pred", A.take(n * 4));
@@ -253,6 +255,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
     D.m = p.m; D.iters = p.iterations; D.ls_k = z.ls_k;
     D.degree_target = p.degree_target; D.local_search = p.local_search;
     D.baseline_scope = p.baseline_scope; D.symmetrize = in.symmetrize; D.h_half = in.h_dtype;
+    D.schedule = p.schedule;
     D.seed = p.seed;
     D.nnz = (int32_t)z.nnz;
     D.alpha = p.alpha; D.beta = p.beta; D.rho = p.rho; D.theta_h = p.theta_h; D.eps = p.eps;
@@ -270,7 +273,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
         SETP(tau, float *) SETP(choice, float *) SETP(nbr, int32_t *) SETP(nbrd, double *)
         SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
         SETP(nbrd32, float *) SETP(ls_el, float *)
-        SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *)
+        SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *) SETP(rb_tour, int32_t *)
         SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
         SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)
         SETP(fbcnt, int32_t *)

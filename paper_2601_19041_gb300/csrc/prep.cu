@@ -793,6 +793,9 @@ __global__ void k_init_bounds(const DevInst *insts)
         st->L_gb = st->L_nn;
         st->L_ib = 0.0;
         st->t = 0; st->ib = -1; st->active = 0; st->n_fallback = 0;
+        st->L_rb = __longlong_as_double(0x7ff0000000000000ll);   // no restart-best yet
+        st->L_dep = 0.0; st->t_restart = 0; st->t_rbimp = 0; st->u_gb = 25; st->n_restarts = 0;
+        st->bf_count = 0;
     }
     for (int s = threadIdx.x; s < I.n; s += blockDim.x) I.gb_tour[s] = I.nn_tour[s];
 }

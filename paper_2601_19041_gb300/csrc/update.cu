@@ -36,8 +36,17 @@ __global__ void k_update(const DevInst *insts, const int2 *slotmap)
     const int j = I.cand[s];
     if (j < 0) return;
     const float omega = __double2float_rn(__dsub_rn(1.0, I.rho));
-    const float delta = __double2float_rn(__ddiv_rn(1.0, st->L_ib));
+    const float delta = __double2float_rn(__ddiv_rn(1.0, st->L_dep));
     I.choice[s] = update_slot(I, s, (int)(s / I.k_pad), j, omega, delta, st->tau_min, st->tau_max);
+}
+
+// MMAS schedule end (restart check, next u_gb); one block per instance
+__global__ void k_schedule(const DevInst *insts)
+{
+    const DevInst &I = insts[blockIdx.x];
+    InstState *st = I.st;
+    if (!st->active || !I.schedule) return;
+    block_schedule_end(I, st);
 }
 
 void launch_two_opt_ib(const DevInst *d_inst, int count, int max_n, cudaStream_t s);
@@ -49,7 +58,8 @@ int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotma
     if (any_ls) launch_two_opt_ib(d_inst, count, max_n, s);
     k_gb<<<count, 256, 0, s>>>(d_inst);
     k_update<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
-    return any_ls ? 4 : 3;
+    k_schedule<<<count, 256, 0, s>>>(d_inst);
+    return any_ls ? 5 : 4;
 }
 
 }  // namespace hac

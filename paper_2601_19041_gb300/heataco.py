@@ -20,7 +20,8 @@ HAC_OK, HAC_EINVAL, HAC_ENOMEM, HAC_ECUDA, HAC_ETIMEOUT, HAC_EUNSUPPORTED, HAC_E
 FIELDS = dict(CAND=1, CDIST=2, CONF=3, BASE=4, EVID=5, W=6, TAU=7, CHOICE=8, NN_TOUR=9,
               GB_TOUR=10, IB_TOUR=11, TOURS=12, LENS=13, SCALARS=14, NBR=15, TRACE=16)
 SCALAR_KEYS = ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
-               "tau_min", "L_gb", "L_ib", "n_lambda", "t", "ib", "n_fallback", "k_pad")
+               "tau_min", "L_gb", "L_ib", "n_lambda", "t", "ib", "n_fallback", "k_pad", "L_rb", "n_restarts",
+               "t_restart", "u_gb")
 
 
 class HeatACOError(RuntimeError):
@@ -45,7 +46,8 @@ class hac_params(C.Structure):
                 ("theta_h", C.c_double), ("eps", C.c_double), ("c_cap", C.c_double),
                 ("q_level", C.c_double), ("p_best", C.c_double), ("logw_clip", C.c_double),
                 ("degree_target", C.c_int32), ("local_search", C.c_int32),
-                ("baseline_scope", C.c_int32), ("ls_k", C.c_int32), ("seed", C.c_uint64)]
+                ("baseline_scope", C.c_int32), ("ls_k", C.c_int32), ("schedule", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class hac_exec(C.Structure):
@@ -183,7 +185,7 @@ class _Marshal:
 def to_c_params(p) -> hac_params:
     return hac_params(p.m, p.k, p.iterations, p.alpha, p.beta, p.rho, p.theta_h, p.eps, p.c_cap,
                       p.q_level, p.p_best, p.logw_clip, p.degree_target, p.local_search,
-                      p.baseline_scope, p.ls_k, p.seed)
+                      p.baseline_scope, p.ls_k, getattr(p, "schedule", 0), p.seed)
 
 
 def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0, profile=0,
@@ -280,8 +282,8 @@ class Batch:
             "TAU": (np.float32, (n, kp)), "CHOICE": (np.float32, (n, kp)),
             "NN_TOUR": (np.int32, (n,)), "GB_TOUR": (np.int32, (n,)), "IB_TOUR": (np.int32, (n,)),
             "TOURS": (np.int32, (m, n)), "LENS": (np.float64, (m,)),
-            "SCALARS": (np.float64, (16,)), "NBR": (np.int32, (n, p.ls_k)),
-            "TRACE": (np.float64, (max(p.iterations, 1), 3)),
+            "SCALARS": (np.float64, (20,)), "NBR": (np.int32, (n, p.ls_k)),
+            "TRACE": (np.float64, (max(p.iterations, 1), 5)),
         }[field]
 
     def read(self, b: int, field: str):

@@ -221,3 +221,49 @@ def test_full_size_tsp10k_two_opt_sampled(hac, orc):
         assert D_ok
     finally:
         bt.close()
+
+
+# ------------------------------------------------------------------ MMAS schedule (Sec. III-B)
+
+def _schedule_batch():
+    rng = np.random.default_rng(3)
+    insts = [euclid(rng.random((10, 2))),                                  # restarts within 700 iterations
+             synth.euclid_instance(81, 60, K=10),
+             synth.atsp_instance(82, 14, K=8),
+             synth.euclid_instance(83, 40, K=10)]
+    ps = [params(m=10, k=8, iterations=700, rho=0.2, seed=5, schedule=1),
+          params(m=12, k=10, iterations=420, rho=0.2, seed=6, schedule=1),
+          params(m=8, k=6, iterations=650, rho=0.2, degree_target=1, seed=7, schedule=1),
+          params(m=8, k=10, iterations=400, rho=0.2, local_search=1, ls_k=10, seed=8, schedule=1)]
+    return insts, ps
+
+
+@pytest.mark.parametrize("ex", [dict(apw=4, fused=1, fbl=32, clog=0), dict(apw=32, fused=1, fbl=32, clog=1),
+                                dict(apw=2, fused=0, fbl=32, clog=0), dict(apw=1, fused=0, fbl=0, clog=0)],
+                         ids=lambda e: f"apw{e['apw']}_fused{e['fused']}_C{1 << e['clog']}")
+def test_mmas_schedule_parity(hac, orc, ex):
+    """Restart-best tour, u_gb elite choice, branching-factor restarts: the
+    per-iteration trace (ib ant, L_ib, L_gb, L_rb, elite/restart code), the
+    pheromone and T_gb bit-exact against the oracle."""
+    insts, ps = _schedule_batch()
+    run_case(hac, orc, insts, ps,
+             exec_=hac.make_exec(ex["apw"], 8 if not ex["fused"] else 0, 1, fused=ex["fused"],
+                                 fallback_list=ex["fbl"], cluster_log2=ex["clog"]))
+    bt = hac.Batch(insts, ps, hac.make_exec(ex["apw"], 8 if not ex["fused"] else 0, 1, fused=ex["fused"],
+                                            fallback_list=ex["fbl"], cluster_log2=ex["clog"]))
+    try:
+        bt.run().sync()
+        restarts = 0
+        for b in range(len(insts)):
+            o = orc.Oracle(insts[b], ps[b]).iterate(ps[b].iterations)
+            tr = bt.read(b, "TRACE")
+            I = ps[b].iterations
+            assert np.array_equal(tr[:I, 3], o.get("trace_Lrb")[:I]), b
+            assert np.array_equal(tr[:I, 4].astype(np.int64), o.get("trace_code")[:I]), b
+            gs = bt.scalars(b)
+            assert gs["n_restarts"] == o.ints()["n_restarts"]
+            assert gs["u_gb"] == o.ints()["u_gb"] and gs["t_restart"] == o.ints()["t_restart"]
+            restarts += int(gs["n_restarts"])
+        assert restarts >= 1
+    finally:
+        bt.close()
