@@ -49,7 +49,7 @@ typedef struct {
     double alpha, beta, rho;
     double theta_h, eps, c_cap, q_level, p_best, logw_clip;
     int32_t degree_target;   /* d* of Sec. III-C: 2 symmetric, 1 ATSP */
-    int32_t local_search;    /* 0 none, 1 2-opt on the iteration-best tour */
+    int32_t local_search;    /* 0 none, 1 2-opt on the iteration-best tour, 2 on every ant's tour */
     int32_t baseline_scope;  /* 0 order statistic over C_i, 1 over the whole heatmap row */
     int32_t ls_k;            /* geometric neighbour-list size of the 2-opt */
     int32_t schedule;        /* 0: T+ = T_ib always; 1: MMAS u_gb schedule and restarts */
@@ -738,11 +738,16 @@ static void iterate_once(orc_state *S)
 {
     int n = S->n, m = S->p.m, kp = S->k_pad;
     for (int a = 0; a < m; ++a) construct(S, a, S->tours + (int64_t)a * n, &S->lens[a]);
+    if (S->p.local_search == 2)                          /* Alg. 1 line 10: 2-opt on every ant */
+        for (int a = 0; a < m; ++a) {
+            orc_two_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
+            S->lens[a] = orc_tour_length(&S->in, S->tours + (int64_t)a * n);
+        }
     int ib = 0;                                          /* iteration best, ties -> lowest ant */
     for (int a = 1; a < m; ++a) if (S->lens[a] < S->lens[ib]) ib = a;
     memcpy(S->ib_tour, S->tours + (int64_t)ib * n, (size_t)n * sizeof(int32_t));
     S->L_ib = S->lens[ib];
-    if (S->p.local_search) {                             /* 2-opt on T_ib before it is used */
+    if (S->p.local_search == 1) {                        /* 2-opt on T_ib before it is used */
         orc_two_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
         S->L_ib = orc_tour_length(&S->in, S->ib_tour);
     }
@@ -832,6 +837,7 @@ static int check_inputs(const orc_instance *in, const orc_params *p)
     }
     if (p->rho <= 0.0 || p->rho >= 1.0 || p->degree_target < 1) return ORC_EINVAL;
     if (p->schedule != 0 && p->schedule != 1) return ORC_EINVAL;
+    if (p->local_search < 0 || p->local_search > 2) return ORC_EINVAL;
     if (p->local_search && (in->kind != 0 || p->ls_k < 1 || p->ls_k > in->n - 1)) return ORC_EINVAL;
     return ORC_OK;
 }

@@ -292,3 +292,25 @@ def test_local_search_run_keeps_invariants(orc):
     assert _two_opt_gain_left(D, ib, nbr) <= 1e-9
     assert o.scalars()["L_ib"] == strided_partials_len(D, ib)
     assert o.scalars()["L_gb"] <= s0["L_nn"]
+
+
+def test_local_search_on_every_ant(orc):
+    # Alg. 1 line 10 with local_search = 2: every ant's tour is 2-opted before
+    # the iteration best is taken; lengths are those of the improved tours
+    from paper_2601_19041_gb300 import synth
+    inst = synth.euclid_instance(92, 150, K=10)
+    p = params(m=6, k=10, iterations=4, rho=0.2, local_search=2, ls_k=10, seed=6)
+    o = orc.Oracle(inst, p)
+    D = dmat(inst.coords)
+    nbr = o.get("nbr")
+    o.iterate(p.iterations)
+    tours, lens = o.get("tours"), o.get("lens")
+    for a in range(p.m):
+        assert is_perm(tours[a], inst.n)
+        assert _two_opt_gain_left(D, tours[a], nbr) <= 1e-9
+        assert lens[a] == strided_partials_len(D, tours[a])
+    ib = int(np.argmin(lens))
+    assert np.array_equal(o.get("ib_tour"), tours[ib])
+    assert o.scalars()["L_ib"] == lens[ib]
+    s = o.scalars()
+    assert s["Rhat"] == 300 and s["tau_max64"] / s["tau_min64"] == pytest.approx(300, rel=1e-13)
