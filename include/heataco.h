@@ -85,7 +85,11 @@ typedef struct {
  *                   paper says "a large constant"; default 30).
  *   local_search    0 none; 1 first-improvement 2-opt with geometric
  *                   neighbour lists and don't-look bits (Sec. III-D) on the
- *                   iteration-best tour and on T_NN; tau_min = tau_max/(2n).
+ *                   iteration-best tour and on T_NN; 2 the same 2-opt on
+ *                   every ant's tour right after its construction (Alg. 1
+ *                   line 10) and on T_NN; tau_min = tau_max/(2n) for both.
+ *                   Mode 2 is not available with 32 ants per warp
+ *                   (HAC_EUNSUPPORTED).
  *   baseline_scope  0: order statistic b_i over the candidates C_i; 1: over all
  *                   heatmap entries of row i (eq. background).
  *   schedule        0 (default): T+ = the iteration-best tour every iteration;

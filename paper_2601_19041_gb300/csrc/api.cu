@@ -37,6 +37,7 @@ struct hac_batch {
     int *d_err = nullptr;
     int max_n = 0, max_kp = 0;
     bool any_ls = false;
+    int ls_all_m = 0;               // largest m among the instances with 2-opt on every ant
     std::vector<int> t_host;
     cudaGraphExec_t gexec = nullptr;
     int graph_kernels = 0;          // kernels inside one graph replay
@@ -178,6 +179,9 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     if (ex.warps_per_block < 1 || ex.warps_per_block > 8) return HAC_EINVAL;
     if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
     if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
+    if (ex.ants_per_warp == 32)   // step-major tours: 2-opt on every ant needs them ant by ant
+        for (int b = 0; b < count; ++b)
+            if (ps[b].local_search == 2) return HAC_EUNSUPPORTED;
 
     hac_batch *bt = new (std::nothrow) hac_batch;
     if (!bt) return HAC_ENOMEM;
@@ -223,6 +227,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
         bt->max_n = std::max(bt->max_n, z.n);
         bt->max_kp = std::max(bt->max_kp, z.kp);
         bt->any_ls |= z.ls != 0;
+        if (z.ls == 2) bt->ls_all_m = std::max(bt->ls_all_m, z.m);
     }
     // work tables
     std::vector<int2> rowmap, slotmap;
@@ -288,7 +293,7 @@ static int enqueue_iteration(hac_batch *bt)
     });
     k += timed(bt, 1, [&] {
         return launch_iteration_tail(bt->d_inst, bt->count, bt->d_slotmap, bt->slotmap_len,
-                                     bt->any_ls, bt->max_n, bt->stream);
+                                     bt->any_ls, bt->max_n, bt->ls_all_m, bt->stream);
     });
     return k;
 }

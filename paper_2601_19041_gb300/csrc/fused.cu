@@ -124,12 +124,22 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
         }
         __syncthreads();
         fallback_distances(I, a_lo, a_hi);     // this CTA's ants only: no cluster barrier needed
-        ant_lengths(I, a_lo, a_hi);
+        if (I.local_search == 2) {             // Alg. 1 line 10: 2-opt on every ant, each warp its own
+            for (int a = a_first; a < min(a_first + APW, a_hi); ++a) {
+                int32_t *tour = I.tours + (size_t)a * n;
+                warp_two_opt(I, tour, ls_ant(I, a));
+                const double L = warp_tour_length(I, tour);
+                if (lane == 0) I.lens[a] = L;
+            }
+            __syncthreads();
+        } else {
+            ant_lengths(I, a_lo, a_hi);
+        }
         __threadfence();
         cl.sync();
         if (rank == 0) {
             block_iteration_best(I, st);
-            if (I.local_search) {
+            if (I.local_search == 1) {
                 if (wib == 0) {
                     warp_two_opt(I, I.ib_tour, ls_global(I, I.ib_tour));
                     const double L = warp_tour_length(I, I.ib_tour);

@@ -67,6 +67,9 @@ struct DevInst {
     double *nbrd;             // n*ls_k their d_ij
     float *nbrd32;            // n*ls_k fl32(d_ij) (2-opt FP32 pre-test)
     float *ls_el;             // n, 2-opt FP32 edge lengths by position (when not in shared memory)
+    int32_t *lsa_pos;         // m*n, 2-opt of every ant (local_search = 2): positions of ant a at a*n
+    float *lsa_el;            // m*n, its FP32 edge lengths
+    uint8_t *lsa_dlb;         // m*n, its don't-look bits
     int32_t *ls_pos;          // n, 2-opt position index
     uint8_t *ls_dlb;          // n, don't-look bits
     int32_t *fbl;             // n*fbl_len (nearest-unvisited lookup list)
@@ -250,7 +253,7 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
 int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
                      int warps_per_block, int max_n, int max_kp, int count, cudaStream_t s);
 int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
-                          int slotmap_len, bool any_ls, int max_n, cudaStream_t s);
+                          int slotmap_len, bool any_ls, int max_n, int ls_all_m, cudaStream_t s);
 // fused cluster kernel (fused.cu): one cluster of 2^clog CTAs per instance;
 // d_iters (parallel to d_order, may be null) gives each cluster its own
 // iteration count instead of `iters`

@@ -61,7 +61,7 @@ inline int check_params(const hac_instance &in, const hac_params &p)
     if (!(p.c_cap >= 0.0) || !(p.logw_clip > 0.0)) return HAC_EINVAL;
     if (p.baseline_scope != 0 && p.baseline_scope != 1) return HAC_EINVAL;
     if (p.schedule != 0 && p.schedule != 1) return HAC_EINVAL;
-    if (p.local_search != 0 && p.local_search != 1) return HAC_EINVAL;
+    if (p.local_search < 0 || p.local_search > 2) return HAC_EINVAL;
     if (p.local_search) {
         if (in.kind != 0) return HAC_EUNSUPPORTED;
         if (p.ls_k < 1 || p.ls_k > 32 || p.ls_k > in.n - 1) return HAC_EINVAL;
@@ -161,6 +161,11 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
         put("ls_pos", A.take(n * 4));
         put("ls_el", A.take(n * 4));
         put("ls_dlb", A.take(n));
+        if (z.ls == 2) {   // every ant's 2-opt: its own positions, edge lengths, bits
+            put("lsa_pos", A.take((size_t)z.m * n * 4));
+            put("lsa_el", A.take((size_t)z.m * n * 4));
+            put("lsa_dlb", A.take((size_t)z.m * n));
+        }
     }
     put("fbl", A.take(n * FBL_LEN * 4));
     put("nn_tour", A.take(n * 4));
@@ -273,6 +278,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
         SETP(tau, float *) SETP(choice, float *) SETP(nbr, int32_t *) SETP(nbrd, double *)
         SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
         SETP(nbrd32, float *) SETP(ls_el, float *)
+        SETP(lsa_pos, int32_t *) SETP(lsa_el, float *) SETP(lsa_dlb, uint8_t *)
         SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *) SETP(rb_tour, int32_t *)
         SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
         SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)

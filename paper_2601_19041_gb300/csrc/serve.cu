@@ -308,6 +308,7 @@ int enqueue_step_route(hac_server *sv, const std::vector<int> &mem, int par)
     size_t nw = 0, ns = 0;
     int it = sv->cfg.iters_per_tick, max_n = 0, max_kp = 0;
     bool any_ls = false;
+    int ls_all_m = 0;
     for (size_t b = 0; b < mem.size(); ++b) {
         const Slot &S = sv->slots[mem[b]];
         hI[b] = sv->hi[mem[b]];
@@ -318,6 +319,7 @@ int enqueue_step_route(hac_server *sv, const std::vector<int> &mem, int par)
         max_n = std::max(max_n, S.z.n);
         max_kp = std::max(max_kp, S.z.kp);
         any_ls |= S.z.ls != 0;
+        if (S.z.ls == 2) ls_all_m = std::max(ls_all_m, S.z.m);
     }
     const int count = (int)mem.size();
     cudaStream_t ss = sv->sstream;
@@ -330,7 +332,7 @@ int enqueue_step_route(hac_server *sv, const std::vector<int> &mem, int par)
         sv->launches += launch_construct(sv->d_sinst[par], sv->d_swarp[par], (int)nw, apw,
                                          sv->sex.warps_per_block, max_n, max_kp, count, ss);
         sv->launches += launch_iteration_tail(sv->d_sinst[par], count, sv->d_sslot[par], (int)ns, any_ls, max_n,
-                                              ss);
+                                              ls_all_m, ss);
     }
     CK(cudaGetLastError());
     for (int q : mem) sv->slots[q].t += it;
@@ -466,6 +468,7 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     if ((st = check_host_data(*in))) return st;
     const int route = sv->cfg.step_min_n > 0 && z.n >= sv->cfg.step_min_n ? 1 : 0;
     if (!route && (st = fits_fused(sv, z))) return st;
+    if (!route && sv->ex.ants_per_warp == 32 && z.ls == 2) return HAC_EUNSUPPORTED;   // step-major tours
     int q = 0;
     while (q < sv->cfg.max_slots && sv->slots[q].state != R_FREE) ++q;
     if (q == sv->cfg.max_slots) return HAC_EBUSY;

@@ -9,7 +9,7 @@ __global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
     extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x];
     if (!I.local_search) return;
-    warp_two_opt(I, I.nn_tour, ls_shared(I, I.nn_tour, ls_sm, smem_bytes));
+    warp_two_opt(I, I.nn_tour, ls_shared(I, I.nn_tour, ls_sm, smem_bytes, ls_global(I, I.nn_tour)));
     const double L = warp_tour_length(I, I.nn_tour);
     if (threadIdx.x == 0) I.st->L_nn = L;
 }
@@ -18,10 +18,24 @@ __global__ void k_two_opt_ib(const DevInst *insts, unsigned smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x];
-    if (!I.local_search || !I.st->active) return;
-    warp_two_opt(I, I.ib_tour, ls_shared(I, I.ib_tour, ls_sm, smem_bytes));
+    if (I.local_search != 1 || !I.st->active) return;
+    warp_two_opt(I, I.ib_tour, ls_shared(I, I.ib_tour, ls_sm, smem_bytes, ls_global(I, I.ib_tour)));
     const double L = warp_tour_length(I, I.ib_tour);
     if (threadIdx.x == 0) I.st->L_ib = L;
+}
+
+// local_search = 2 (Alg. 1 line 10): ant blockIdx.x % max_m of instance
+// blockIdx.x / max_m, right after construction; its length is recomputed
+__global__ void k_two_opt_all(const DevInst *insts, int max_m, unsigned smem_bytes)
+{
+    extern __shared__ __align__(16) unsigned char ls_sm[];
+    const DevInst &I = insts[blockIdx.x / max_m];
+    const int a = blockIdx.x % max_m;
+    if (I.local_search != 2 || a >= I.m || I.st->t >= I.iters) return;
+    int32_t *tour = I.tours + (size_t)a * I.n;
+    warp_two_opt(I, tour, ls_shared(I, tour, ls_sm, smem_bytes, ls_ant(I, a)));
+    const double L = warp_tour_length(I, tour);
+    if (threadIdx.x == 0) I.lens[a] = L;
 }
 
 // shared memory sized for the largest instance, capped (each instance then
@@ -39,6 +53,14 @@ static void ls_launch(Kern kern, const DevInst *d_inst, int count, int max_n, cu
     const size_t smem = ls_launch_smem(max_n);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<count, 32, smem, s>>>(d_inst, (unsigned)smem);
+}
+
+void launch_two_opt_all(const DevInst *d_inst, int count, int max_m, int max_n, cudaStream_t s)
+{
+    const size_t smem = ls_launch_smem(max_n);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_two_opt_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_two_opt_all<<<count * max_m, 32, smem, s>>>(d_inst, max_m, (unsigned)smem);
 }
 
 void launch_two_opt_nn(const DevInst *d_inst, int count, int max_n, cudaStream_t s)

@@ -277,17 +277,25 @@ __device__ __forceinline__ LsMem ls_global(const DevInst &I, int32_t *tour)
     return LsMem{tour, I.ls_pos, I.ls_dlb, I.ls_el, reinterpret_cast<const float2 *>(I.xy)};
 }
 
+// the workspace arrays of ant a's own search (local_search = 2; ant-major tours)
+__device__ __forceinline__ LsMem ls_ant(const DevInst &I, int a)
+{
+    const size_t o = (size_t)a * I.n;
+    return LsMem{I.tours + o, I.lsa_pos + o, I.lsa_dlb + o, I.lsa_el + o, reinterpret_cast<const float2 *>(I.xy)};
+}
+
 // shared memory: tour, pos, el (4n bytes each), dlb (n bytes), then the
 // coordinates at a 16-byte boundary when they fit as well
 __host__ __device__ inline size_t ls_smem_core(int n) { return (size_t)n * 13; }
 __host__ __device__ inline size_t ls_xy_offset(int n) { return ((size_t)n * 13 + 15) & ~(size_t)15; }
 __host__ __device__ inline size_t ls_smem_full(int n) { return ls_xy_offset(n) + (size_t)n * 8; }
 
-// arrays in `sm` (smem_bytes) where they fit, else in the workspace; one warp
-__device__ __forceinline__ LsMem ls_shared(const DevInst &I, int32_t *tour, unsigned char *sm, size_t smem_bytes)
+// arrays in `sm` (smem_bytes) where they fit, else `fallback`; one warp
+__device__ __forceinline__ LsMem ls_shared(const DevInst &I, int32_t *tour, unsigned char *sm, size_t smem_bytes,
+                                           const LsMem &fallback)
 {
     const int n = I.n;
-    if (ls_smem_core(n) > smem_bytes) return ls_global(I, tour);
+    if (ls_smem_core(n) > smem_bytes) return fallback;
     LsMem M;
     M.tour = reinterpret_cast<int32_t *>(sm);
     M.pos = reinterpret_cast<int32_t *>(sm + (size_t)n * 4);

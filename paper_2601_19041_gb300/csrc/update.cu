@@ -50,16 +50,18 @@ __global__ void k_schedule(const DevInst *insts)
 }
 
 void launch_two_opt_ib(const DevInst *d_inst, int count, int max_n, cudaStream_t s);
+void launch_two_opt_all(const DevInst *d_inst, int count, int max_m, int max_n, cudaStream_t s);
 
 int launch_iteration_tail(const DevInst *d_inst, int count, const int2 *d_slotmap,
-                          int slotmap_len, bool any_ls, int max_n, cudaStream_t s)
+                          int slotmap_len, bool any_ls, int max_n, int ls_all_m, cudaStream_t s)
 {
+    if (ls_all_m > 0) launch_two_opt_all(d_inst, count, ls_all_m, max_n, s);
     k_select<<<count, 256, 0, s>>>(d_inst);
     if (any_ls) launch_two_opt_ib(d_inst, count, max_n, s);
     k_gb<<<count, 256, 0, s>>>(d_inst);
     k_update<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
     k_schedule<<<count, 256, 0, s>>>(d_inst);
-    return any_ls ? 5 : 4;
+    return (any_ls ? 5 : 4) + (ls_all_m > 0 ? 1 : 0);
 }
 
 }  // namespace hac

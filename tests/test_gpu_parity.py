@@ -267,3 +267,27 @@ def test_mmas_schedule_parity(hac, orc, ex):
         assert restarts >= 1
     finally:
         bt.close()
+
+
+# ------------------------------------------------------------------ 2-opt on every ant (Alg. 1 line 10)
+
+@pytest.mark.parametrize("ex", [dict(apw=4, fused=1, clog=0), dict(apw=2, fused=1, clog=1),
+                                dict(apw=4, fused=0, clog=0), dict(apw=1, fused=0, clog=0)],
+                         ids=lambda e: f"apw{e['apw']}_fused{e['fused']}_C{1 << e['clog']}")
+def test_two_opt_every_ant_parity(hac, orc, ex):
+    insts = [synth.euclid_instance(91, 300, K=10), synth.euclid_instance(92, 77, K=10),
+             synth.euclid_instance(93, 150, K=20)]
+    ps = [params(m=9, k=10, iterations=5, rho=0.2, local_search=2, ls_k=10, seed=21),
+          params(m=6, k=8, iterations=40, rho=0.2, local_search=2, ls_k=8, seed=22, schedule=1),
+          params(m=5, k=12, iterations=6, rho=0.2, local_search=0, seed=23)]
+    run_case(hac, orc, insts, ps,
+             exec_=hac.make_exec(ex["apw"], 8 if not ex["fused"] else 0, 1, fused=ex["fused"], fallback_list=32,
+                                 cluster_log2=ex["clog"]))
+
+
+def test_two_opt_every_ant_rejects_lane_mode(hac):
+    inst = synth.euclid_instance(94, 50, K=10)
+    p = params(m=4, k=8, iterations=2, rho=0.2, local_search=2, ls_k=8, seed=1)
+    with pytest.raises(hac.HeatACOError) as e:
+        hac.Batch([inst], [p], hac.make_exec(32, 0, 1, fused=1))
+    assert e.value.status == hac.HAC_EUNSUPPORTED
