@@ -48,6 +48,12 @@ WORKLOAD_TEXT = {
                 "m=50, k=20, rho=0.2, d*=1, 200 iterations",
     "tsp10k_2opt": "16 symmetric TSP instances, n=10000, 10-NN heatmap; m=64, k=10, rho=0.2, "
                    "300 iterations, 2-opt on the iteration-best tour",
+    "paper_tsp500": "paper setting (Sec. IV-D): 128 symmetric TSP instances, n=500, 50-NN heatmap; m=32, k=20, "
+                    "rho=0.8, 5000 iterations, MMAS u_gb schedule and restarts, no local search",
+    "paper_tsp500_2opt": "paper setting: 128 instances, n=500; m=32, k=20, rho=0.8, 5000 iterations, MMAS schedule, "
+                         "2-opt (20-NN lists, don't-look bits) on every ant's tour",
+    "paper_tsp1k": "paper setting: 128 symmetric TSP instances, n=1000, 50-NN heatmap; m=32, k=20, rho=0.8, "
+                   "5000 iterations, MMAS schedule, no local search",
     "serve": "Poisson arrivals (default 200 req/s) of decode requests, n from {500,1000,2000,5000,10000}, "
              "points uniform / 8-cluster Gaussian mixture (sigma 0.05) / perturbed grid (jitter 0.1), "
              "50-NN heatmaps stored FP16, m=64, k=20, rho=0.2, 100-300 iterations",
@@ -103,7 +109,8 @@ def load_peaks():
 
 
 def workload(name, rank):
-    base = {"batch128": 1000, "atsp1000": 3000, "tsp10k_2opt": 2000, "tsp500": None}[name]
+    base = {"batch128": 1000, "atsp1000": 3000, "tsp10k_2opt": 2000, "tsp500": None,
+            "paper_tsp500": 5000, "paper_tsp500_2opt": 5000, "paper_tsp1k": 6000}[name]
     if name == "tsp500" or rank == 0:
         return synth.workload(name)
     return synth.workload(name, base_seed=base + 100000 * rank)

@@ -26,7 +26,11 @@ import numpy as np
 
 # the five synthetic workloads: symmetric n=500; batched n~U{500..2000};
 # large n=10000 with 2-opt; ATSP n=1000; a serving stream of mixed sizes.
-WORKLOADS = ("tsp500", "batch128", "tsp10k_2opt", "atsp1000", "serve")
+# Paper-setting runs (Sec. IV-D parameters: m=32, k=20, I=5000, rho=0.8, the
+# MMAS schedule) on 128 instances of n=500 or n=1000, without local search
+# and with 2-opt on every ant, for comparison with the paper's decode times.
+WORKLOADS = ("tsp500", "batch128", "tsp10k_2opt", "atsp1000", "serve",
+             "paper_tsp500", "paper_tsp500_2opt", "paper_tsp1k")
 
 
 @dataclass
@@ -212,6 +216,15 @@ def workload(name: str, count: int | None = None, base_seed: int | None = None):
         b0 = 3000 if base_seed is None else base_seed
         inst = [atsp_instance(b0 + b, 1000, K=50) for b in range(cnt)]
         ps = [Params(m=50, k=20, iterations=200, rho=0.2, degree_target=1, seed=b0 + b)
+              for b in range(cnt)]
+        return inst, ps
+    if name in ("paper_tsp500", "paper_tsp500_2opt", "paper_tsp1k"):
+        cnt = 128 if count is None else count
+        n = 1000 if name == "paper_tsp1k" else 500
+        b0 = (6000 if n == 1000 else 5000) if base_seed is None else base_seed
+        ls = 2 if name.endswith("2opt") else 0
+        inst = [euclid_instance(b0 + b, n, K=50) for b in range(cnt)]
+        ps = [Params(m=32, k=20, iterations=5000, rho=0.8, local_search=ls, ls_k=20, schedule=1, seed=b0 + b)
               for b in range(cnt)]
         return inst, ps
     raise ValueError(name)
