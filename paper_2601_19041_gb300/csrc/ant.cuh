@@ -19,7 +19,6 @@
 // unvisited bits of the ant's mask.
 #pragma once
 
-#include "grid.cuh"
 #include "lengths.cuh"
 
 namespace hac {
@@ -154,9 +153,7 @@ struct ClusterList {
 // a < a_end) in iteration t.  vis_warp: APW bitmasks of `stride` words.
 // Tours (and the chosen slot of every step, 0xff for a nearest-unvisited
 // step) are written ant-major; lengths are summed afterwards (lengths.cuh).
-// GRID: after a lookup-list miss, the ring search of grid.cuh (instances that
-// have a grid) instead of the scan; compiled in only where such instances run.
-template <int APW, typename Rows, typename List, bool GRID = false>
+template <int APW, typename Rows, typename List>
 __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, const List &list, int t,
                                             int a_first, int a_end, unsigned *vis_warp, int stride,
                                             const float2 *xy_scan)
@@ -173,8 +170,6 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
     const float2 *__restrict__ xy = xy_scan;   // coordinates for the fallback scan
     const int nwords = (n + 31) >> 5;
     unsigned *vis = vis_warp + seg * stride;
-    GridView gv{};
-    if constexpr (GRID) gv = GridView{I.gstart, I.gnode, kind == 0 ? I.grid_g : 0, I.st->gx0, I.st->gy0, I.st->gcs};
 
     for (int w = sl; w <= (n >> 5); w += SEG) vis[w] = 0u;   // bits 0..n
     __syncwarp();
@@ -282,8 +277,6 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
                 const unsigned bm = __ballot_sync(FULL_MASK, ok);
                 if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
             }
-            if constexpr (GRID)
-                if (found < 0 && gv.G > 0) found = grid_nearest(gv, xy, scur, sv, 1, 0);
             if (found < 0) {
                 float bk = __int_as_float(0x7f800000);
                 int bu = 0x7fffffff;

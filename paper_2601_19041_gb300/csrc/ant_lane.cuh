@@ -26,7 +26,7 @@
 namespace hac {
 
 
-template <int NG, typename Rows, typename List, bool GRID = false>
+template <int NG, typename Rows, typename List>
 __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &rows, const List &list,
                                                  int t, int a_first, int a_end, unsigned *vis_warp,
                                                  const float2 *xy_scan)
@@ -39,8 +39,6 @@ __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &r
     const float *__restrict__ cost = I.cost;
     const float2 *__restrict__ xy = xy_scan;
     const int nwords = (n + 31) >> 5;
-    GridView gv{};
-    if constexpr (GRID) gv = GridView{I.gstart, I.gnode, kind == 0 ? I.grid_g : 0, I.st->gx0, I.st->gy0, I.st->gcs};
     int32_t *__restrict__ tourT = I.tours;      // step-major: [s * m + a]
     uint8_t *__restrict__ slotT = I.slots;      // step-major
     int32_t *__restrict__ fbs = I.fbs + (size_t)(real ? a : 0) * n;
@@ -154,8 +152,6 @@ __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &r
                     const unsigned bm = __ballot_sync(FULL_MASK, ok);
                     if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
                 }
-                if constexpr (GRID)
-                    if (found < 0 && gv.G > 0) found = grid_nearest(gv, xy, scur, vis_warp, 32, L);
                 if (found < 0) {
                     float bk = __int_as_float(0x7f800000);
                     int bu = 0x7fffffff;

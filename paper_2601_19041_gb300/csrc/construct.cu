@@ -6,7 +6,7 @@
 
 namespace hac {
 
-template <int APW, bool GRID>
+template <int APW>
 __global__ void __launch_bounds__(256, 1) k_construct(const DevInst *__restrict__ insts,
                                                    const int4 *__restrict__ warpmap, int nwarps,
                                                    int nwords_max)
@@ -21,13 +21,12 @@ __global__ void __launch_bounds__(256, 1) k_construct(const DevInst *__restrict_
     if (t >= I.iters) return;                       // warp-uniform
     GlobalRows rows{reinterpret_cast<const int4 *>(I.cand), reinterpret_cast<const float4 *>(I.choice),
                     I.k_pad >> 2, I.n};
-    build_tours<APW, GlobalRows, GlobalList, GRID>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m,
-                                                   smem_vis + (size_t)wib * APW * nwords_max, nwords_max,
-                                                   reinterpret_cast<const float2 *>(I.xy));
+    build_tours<APW>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m, smem_vis + (size_t)wib * APW * nwords_max,
+                     nwords_max, reinterpret_cast<const float2 *>(I.xy));
 }
 
 // one ant per lane: warp w of the table builds ants a0..a0+31 of its instance
-template <int NG, bool GRID>
+template <int NG>
 __global__ void __launch_bounds__(256, 1) k_construct_lane(const DevInst *__restrict__ insts,
                                                         const int4 *__restrict__ warpmap, int nwarps,
                                                         int nwords_max)
@@ -42,9 +41,8 @@ __global__ void __launch_bounds__(256, 1) k_construct_lane(const DevInst *__rest
     if (t >= I.iters) return;
     GlobalRows rows{reinterpret_cast<const int4 *>(I.cand), reinterpret_cast<const float4 *>(I.choice),
                     I.k_pad >> 2, I.n};
-    build_tours_lane<NG, GlobalRows, GlobalList, GRID>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m,
-                                                       smem_vis + (size_t)wib * 32 * nwords_max,
-                                                       reinterpret_cast<const float2 *>(I.xy));
+    build_tours_lane<NG>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m, smem_vis + (size_t)wib * 32 * nwords_max,
+                         reinterpret_cast<const float2 *>(I.xy));
 }
 
 // fallback distances, then every ant's length (one block per instance)
@@ -56,27 +54,18 @@ __global__ void k_lengths(const DevInst *insts)
     ant_lengths(I, 0, I.m);
 }
 
-template <int APW, bool GRID>
+template <int APW>
 static void launch_construct_apw(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len,
                                  int warps_per_block, int max_n, cudaStream_t s)
 {
     int nwords = (max_n + 32) / 32;   // visited bits 0..n (n: padding id)
     size_t smem = (size_t)warps_per_block * APW * nwords * sizeof(unsigned);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_construct<APW, GRID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_construct<APW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     int blocks = (warpmap_len + warps_per_block - 1) / warps_per_block;
-    k_construct<APW, GRID><<<blocks, warps_per_block * 32, smem, s>>>(d_inst, d_warpmap, warpmap_len,
-                                                                       nwords);
-}
-
-template <int APW>
-static void launch_construct_g(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len,
-                               int warps_per_block, int max_n, cudaStream_t s)
-{
-    // the ring-search variant only where some instance can have a grid
-    if (max_n >= GRID_MIN_N) launch_construct_apw<APW, true>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
-    else launch_construct_apw<APW, false>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
+    k_construct<APW><<<blocks, warps_per_block * 32, smem, s>>>(d_inst, d_warpmap, warpmap_len,
+                                                                 nwords);
 }
 
 int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_len, int apw,
@@ -92,16 +81,15 @@ int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_l
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             kern<<<blocks, warps_per_block * 32, smem, s>>>(d_inst, d_warpmap, warpmap_len, nwords);
         };
-        const bool grid = max_n >= GRID_MIN_N;
-        if (G <= 3) grid ? go(k_construct_lane<3, true>) : go(k_construct_lane<3, false>);
-        else if (G <= 5) grid ? go(k_construct_lane<5, true>) : go(k_construct_lane<5, false>);
-        else grid ? go(k_construct_lane<8, true>) : go(k_construct_lane<8, false>);
+        if (G <= 3) go(k_construct_lane<3>);
+        else if (G <= 5) go(k_construct_lane<5>);
+        else go(k_construct_lane<8>);
         k_lengths<<<count, 256, 0, s>>>(d_inst);
         return 2;
     }
-    if (apw == 4) launch_construct_g<4>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
-    else if (apw == 2) launch_construct_g<2>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
-    else launch_construct_g<1>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
+    if (apw == 4) launch_construct_apw<4>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
+    else if (apw == 2) launch_construct_apw<2>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
+    else launch_construct_apw<1>(d_inst, d_warpmap, warpmap_len, warps_per_block, max_n, s);
     k_lengths<<<count, 256, 0, s>>>(d_inst);
     return 2;
 }

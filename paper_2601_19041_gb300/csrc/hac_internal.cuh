@@ -17,8 +17,6 @@ namespace hac {
 constexpr int KMAX = HAC_KMAX;
 constexpr double DFLOOR = 1e-9;     // eta = 1/max(d, 1e-9): coincident points
 constexpr double LS_GAIN = 1e-10;   // 2-opt moves need a gain above this
-constexpr size_t GRID_SMEM_MAX = 200 * 1024;   // counting-sort counters of the grid build
-constexpr int GRID_MIN_N = 4096;               // smaller instances scan instead
 constexpr int TRACE_W = 5;          // trace entries per iteration: ib ant, L_ib, L_gb, L_rb, code
 
 // Per-instance scalars that live on the device (read back through HAC_F_SCALARS).
@@ -39,7 +37,6 @@ struct InstState {
     int32_t u_gb;       // T_rb deposits when the iteration is a multiple of this
     int32_t n_restarts;
     unsigned long long bf_count;   // branching-factor count of the current check
-    float gx0, gy0, gcs;           // coordinate grid: origin and cell side
 };
 
 // Device view of one instance: sizes, parameters and pointers into the workspace.
@@ -80,9 +77,6 @@ struct DevInst {
     // search state
     int32_t *nn_tour, *gb_tour, *ib_tour, *succ, *pred;   // n each
     int32_t *rb_tour;         // n, restart-best tour (schedule = 1)
-    int32_t grid_g;           // coordinate grid side G (0: no grid)
-    int32_t *gstart;          // G*G + 1 cell starts into gnode
-    int32_t *gnode;           // n node ids sorted by cell
     int32_t *tours;           // m*n: tour of ant a, step s at a*tour_sa + s*tour_ss
     int32_t tour_sa, tour_ss; // (n, 1) ant-major, or (1, m) step-major (one ant per lane)
     uint8_t *slots;           // m*n chosen slot per step (same layout as tours), 0xff: nearest-unvisited

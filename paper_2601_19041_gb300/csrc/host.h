@@ -40,20 +40,6 @@ struct Arena {
     }
 };
 
-// coordinate grid of the nearest-unvisited search: side G (grid.cuh), used
-// when its counting-sort counters fit the build kernel's shared memory
-inline int grid_side_host(int n)
-{
-    int g = 1;
-    while (2 * g * g < n) ++g;
-    return g;
-}
-inline bool grid_used(int n)
-{
-    const size_t G = (size_t)grid_side_host(n);
-    return n >= GRID_MIN_N && (G * G + 1) * sizeof(int) <= GRID_SMEM_MAX;
-}
-
 struct Sizes {
     int n, kind, kp, k_eff, m, iters, ls, ls_k, sym, half;
     long long nnz;
@@ -182,11 +168,6 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
         }
     }
     put("fbl", A.take(n * FBL_LEN * 4));
-    if (z.kind == 0 && grid_used(z.n)) {
-        const size_t G = (size_t)grid_side_host(z.n);
-        put("gstart", A.take((G * G + 1) * 4));
-        put("gnode", A.take(n * 4));
-    }
     put("nn_tour", A.take(n * 4));
     put("gb_tour", A.take(n * 4));
     put("rb_tour", A.take(n * 4));
@@ -280,7 +261,6 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
     D.degree_target = p.degree_target; D.local_search = p.local_search;
     D.baseline_scope = p.baseline_scope; D.symmetrize = in.symmetrize; D.h_half = in.h_dtype;
     D.schedule = p.schedule;
-    D.grid_g = z.kind == 0 && grid_used(z.n) ? grid_side_host(z.n) : 0;
     D.seed = p.seed;
     D.nnz = (int32_t)z.nnz;
     D.alpha = p.alpha; D.beta = p.beta; D.rho = p.rho; D.theta_h = p.theta_h; D.eps = p.eps;
@@ -299,7 +279,6 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
         SETP(ls_pos, int32_t *) SETP(ls_dlb, uint8_t *) SETP(nn_tour, int32_t *)
         SETP(nbrd32, float *) SETP(ls_el, float *)
         SETP(lsa_pos, int32_t *) SETP(lsa_el, float *) SETP(lsa_dlb, uint8_t *)
-        SETP(gstart, int32_t *) SETP(gnode, int32_t *)
         SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *) SETP(rb_tour, int32_t *)
         SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
         SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)

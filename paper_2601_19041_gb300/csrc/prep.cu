@@ -13,10 +13,8 @@
 // Work decomposition: rows of all instances are spread over warps through a
 // host-built (instance, first row) table; per-instance reductions run one
 // block per instance.
-#include <algorithm>
 #include <cuda_fp16.h>
 
-#include "grid.cuh"
 #include "lengths.cuh"
 
 namespace hac {
@@ -814,73 +812,6 @@ __global__ void k_init_tau(const DevInst *insts, const int2 *slotmap)
     I.choice[s] = real ? choice_of(I, tau, I.W[s]) : 0.0f;
 }
 
-// ------------------------------------------------------------ coordinate grid
-
-// One block per Euclidean instance: bounding box, cell side, then the nodes
-// sorted by cell (counting sort in shared memory: G*G + 1 counters).
-__global__ void k_grid(const DevInst *insts)
-{
-    extern __shared__ int gcnt[];
-    __shared__ float red[4][32];
-    const DevInst &I = insts[blockIdx.x];
-    if (I.kind != 0 || I.grid_g == 0) return;
-    const int n = I.n, G = I.grid_g, L = G * G + 1;
-    const float2 *xy = reinterpret_cast<const float2 *>(I.xy);
-    const float INF = __int_as_float(0x7f800000);
-    float lx = INF, ly = INF, hx = -INF, hy = -INF;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float2 p = xy[i];
-        lx = fminf(lx, p.x); ly = fminf(ly, p.y); hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y);
-    }
-    for (int o = 16; o; o >>= 1) {
-        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (lane == 0) { red[0][w] = lx; red[1][w] = ly; red[2][w] = hx; red[3][w] = hy; }
-    for (int c = threadIdx.x; c < L; c += blockDim.x) gcnt[c] = 0;
-    __syncthreads();
-    lx = ly = INF; hx = hy = -INF;
-    for (int q = 0; q < nw; ++q) {
-        lx = fminf(lx, red[0][q]); ly = fminf(ly, red[1][q]);
-        hx = fmaxf(hx, red[2][q]); hy = fmaxf(hy, red[3][q]);
-    }
-    const float ext = fmaxf(__fsub_rn(hx, lx), __fsub_rn(hy, ly));
-    const float cs = ext > 0.0f ? __fdiv_rn(ext, (float)G) : 1.0f;
-    GridView gv{nullptr, nullptr, G, lx, ly, cs};
-    if (threadIdx.x == 0) { I.st->gx0 = lx; I.st->gy0 = ly; I.st->gcs = cs; }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float2 p = xy[i];
-        atomicAdd(&gcnt[gv.cell_of(p.y, ly) * G + gv.cell_of(p.x, lx) + 1], 1);
-    }
-    __syncthreads();
-    // inclusive scan of gcnt: per-thread chunks, then the chunk totals
-    __shared__ int part[1024];
-    const int per = (L + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per, b1 = min(L, b0 + per);
-    int sum = 0;
-    for (int c = b0; c < b1; ++c) sum += gcnt[c];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int q = 1; q < (int)blockDim.x; ++q) part[q] += part[q - 1];
-    __syncthreads();
-    int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (int c = b0; c < b1; ++c) {
-        run += gcnt[c];
-        gcnt[c] = run;
-        I.gstart[c] = run;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float2 p = xy[i];
-        const int c = gv.cell_of(p.y, ly) * G + gv.cell_of(p.x, lx);
-        I.gnode[atomicAdd(&gcnt[c], 1)] = i;
-    }
-}
-
 // defined in twoopt.cu
 void launch_two_opt_nn(const DevInst *d_inst, int count, int max_n, cudaStream_t s);
 
@@ -917,14 +848,6 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
     k_nn_tour<<<count, 1024, vis_bytes, s>>>(d_inst);
     if (any_ls) { launch_two_opt_nn(d_inst, count, max_n, s); ++launched; }
     k_init_bounds<<<count, 256, 0, s>>>(d_inst);
-    {
-        // counters for the largest instance that has a grid (at most GRID_SMEM_MAX)
-        const int G = grid_side(max_n);
-        const size_t gsm = std::min(((size_t)G * G + 1) * sizeof(int), GRID_SMEM_MAX);
-        if (gsm > 48 * 1024) cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
-        k_grid<<<count, 1024, gsm, s>>>(d_inst);
-        ++launched;
-    }
     k_fbl_check<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
     const int wpw = (max_n + 31) / 32;
     const size_t fbl_smem = (size_t)ROW_WARPS * wpw * sizeof(unsigned);

@@ -291,18 +291,3 @@ def test_two_opt_every_ant_rejects_lane_mode(hac):
     with pytest.raises(hac.HeatACOError) as e:
         hac.Batch([inst], [p], hac.make_exec(32, 0, 1, fused=1))
     assert e.value.status == hac.HAC_EUNSUPPORTED
-
-
-# ------------------------------------------------------------------ grid search of the nearest unvisited node
-
-@pytest.mark.parametrize("apw,fbl", [(1, 0), (4, 32), (32, 0), (2, 0)])
-def test_grid_nearest_unvisited_parity(hac, orc, apw, fbl):
-    """Per-step kernels on instances of n >= 4096 find the nearest unvisited
-    node through the coordinate grid (after a lookup-list miss, or at once
-    without lists): clustered points, a grid with duplicate points, uniform."""
-    insts = [synth.euclid_instance(95, 4500, K=10, family="gmm"),
-             euclid(np.repeat(synth.perturbed_grid_points(np.random.default_rng(96), 2100), 2, axis=0)),
-             synth.euclid_instance(97, 5000, K=10)]
-    ps = [params(m=6, k=10, iterations=3, rho=0.2, seed=31), params(m=5, k=8, iterations=2, rho=0.2, seed=32),
-          params(m=4, k=12, iterations=2, rho=0.2, seed=33)]
-    run_case(hac, orc, insts, ps, exec_=hac.make_exec(apw, 8 if apw != 32 else 2, 1, fused=0, fallback_list=fbl))
