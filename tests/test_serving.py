@@ -37,6 +37,11 @@ def _requests():
     reqs.append((cost, synth.Params(m=20, k=12, iterations=8, rho=0.2, degree_target=1, seed=77)))
     ls = synth.euclid_instance(78, 200, K=10)
     reqs.append((ls, synth.Params(m=16, k=10, iterations=6, rho=0.2, local_search=1, seed=78)))
+    # the MMAS schedule with restarts, and 2-opt on every ant
+    reqs.append((synth.euclid_instance(79, 10, K=5), synth.Params(m=10, k=8, iterations=320, rho=0.2, seed=79,
+                                                                   schedule=1)))
+    reqs.append((synth.euclid_instance(80, 150, K=10), synth.Params(m=8, k=10, iterations=5, rho=0.2, seed=80,
+                                                                    local_search=2, ls_k=10)))
     return reqs
 
 
@@ -57,7 +62,9 @@ def _drain(srv, tickets, out, max_ticks=1000):
                                                    (4, 3, 1500, 300, 1), (32, 4, 0, 100, 2), (4, 5, 0, 3, 4)])
 def test_mix_equals_alone_and_oracle(hac, orc, apw, ipt, spt, smin, sapw):
     reqs = _requests()
-    srv = hac.Server(64 << 20, max_slots=8, iters_per_tick=ipt, max_n=1000, steps_per_tick=spt,
+    if apw == 32:   # 2-opt on every ant needs ant-major tours
+        reqs = [(i, p) for i, p in reqs if p.local_search != 2]
+    srv = hac.Server(64 << 20, max_slots=10, iters_per_tick=ipt, max_n=1000, steps_per_tick=spt,
                      step_min_n=smin, step_ants_per_warp=sapw, step_warps_per_block=4 if sapw == 4 else 8,
                      exec_=hac.make_exec(ants_per_warp=apw, fused=1, fallback_list=32 if apw != 2 else 0))
     try:
