@@ -108,12 +108,31 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def workload(name, rank):
+def workload(name, rank, count=None):
+    """The instances of rank `rank` (weak scaling: every rank decodes a batch of
+    its own, seeds shifted by 100000 per rank; rank 0 holds the 1-GPU batch).
+    tsp500 is one fixed instance, the same on every rank."""
     base = {"batch128": 1000, "atsp1000": 3000, "tsp10k_2opt": 2000, "tsp500": None,
             "paper_tsp500": 5000, "paper_tsp500_2opt": 5000, "paper_tsp1k": 6000}[name]
     if name == "tsp500" or rank == 0:
-        return synth.workload(name)
-    return synth.workload(name, base_seed=base + 100000 * rank)
+        return synth.workload(name, count=count)
+    return synth.workload(name, count=count, base_seed=base + 100000 * rank)
+
+
+def combine_ranks(values, device, ops):
+    """Combines one float per entry across the ranks of the process group
+    (ops: "max" or "sum" per entry); the values themselves when there is no
+    group.  Used for the max-over-ranks device time and the summed work."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    out = []
+    for v, op in zip(values, ops):
+        t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+        out.append(float(t.item()))
+    return out
 
 
 def total_ant_steps(insts, ps, iters=None):
@@ -272,9 +291,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     build.build()
     L = heataco._lib()
-    insts, ps = workload(args.workload, rank)
-    if args.count:
-        insts, ps = insts[:args.count], ps[:args.count]
+    insts, ps = workload(args.workload, rank, count=args.count or None)
     if args.iters:
         for p in ps:
             p.iterations = args.iters
@@ -349,17 +366,9 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t_max = dev_ms
-    total_steps = steps_per * args.steps
+    t_max, total_steps = combine_ranks([dev_ms, steps_per * args.steps], "cuda", ["max", "sum"])
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        s = torch.tensor([total_steps], device="cuda", dtype=torch.float64)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        total_steps = float(s.item())
-        dist.barrier()
+        torch.distributed.barrier()
     value = total_steps / (t_max / 1000.0)
     inst_per_s = count * world * args.steps / (t_max / 1000.0)
 
@@ -433,12 +442,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             e2e_step()
             walls.append(time.perf_counter() - t0)
-        w = sum(walls)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([w], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            w = float(t.item())
+        w, = combine_ranks([sum(walls)], "cuda", ["max"])
         e2e = {"value": steps_per * world * args.steps / w, "unit": "ant-steps/s",
                "h2d_bytes_per_step": input_bytes(insts),
                "d2h_bytes_per_step": int(sum(4 * i.n for i in insts) + 8 * count),
