@@ -99,6 +99,13 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# DRAM bytes per fused launch measured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) for a workload and layout; the summary with its
+# command is in profiles/dram_traffic_batch128_n500-2000.md.  Reported as
+# roofline.traffic only for the same workload and layout.
+NCU_TRAFFIC = {("batch128", 1, 2, 32, 0, 200): 5.372e9 + 6.298e9}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -476,7 +483,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                         "traffic": None,
+                         "traffic": NCU_TRAFFIC.get((args.workload, args.fused, ex.ants_per_warp or 4, args.fbl,
+                                                     args.clog, ps[0].iterations)) if count == 128 else None,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_ms": avg_ms, "share_of_step": construct_share},
             "cpu_baseline": cpu,
