@@ -86,12 +86,14 @@ typedef struct {
  *   local_search    0 none; 1 first-improvement 2-opt with geometric
  *                   neighbour lists and don't-look bits (Sec. III-D) on the
  *                   iteration-best tour and on T_NN; 2 the same 2-opt on
- *                   every ant's tour right after its construction (Alg. 1
- *                   line 10) and on T_NN; tau_min = tau_max/(2n) for both.
+ *                   every ant's tour right after its construction (the
+ *                   local search of Algorithm 1) and on T_NN; tau_min =
+ *                   tau_max/(2n) for both.
  *                   Mode 2 is not available with 32 ants per warp
  *                   (HAC_EUNSUPPORTED).
  *   baseline_scope  0: order statistic b_i over the candidates C_i; 1: over all
- *                   heatmap entries of row i (eq. background).
+ *                   heatmap entries of row i (eq. background defines c on C_i
+ *                   but speaks of "row i"; both readings are offered).
  *   schedule        0 (default): T+ = the iteration-best tour every iteration;
  *                   1: the MMAS machinery of Sec. III-B and Algorithm 1 --
  *                   restart-best tour T_rb, elite T+ = T_rb every u_gb
@@ -137,12 +139,12 @@ int hac_version(void);
 /* ------------------------------------------------------------------ batches
  * A batch is `count` independent instances decoded together on one GPU: each
  * instance has its own parameters (m, k, iterations, seed, ...), pheromone and
- * best-tour state, all resident in the workspace.  Algorithm 1 lines 1-6
- * (preparation: candidate lists of Sec. III-A, evidence and kappa of
- * Sec. III-C, T_NN and the bounds of eq. tau_init / tau_min_nols) run in
- * hac_batch_create; lines 8-21 (construction by Algorithm 2, iteration best,
- * global best with recomputed bounds, bounded evaporation/deposit of eq.
- * pheromone_update) run in hac_batch_iterate. */
+ * best-tour state, all resident in the workspace.  The preparation steps of
+ * Algorithm 1 (candidate lists of Sec. III-A, evidence and kappa of Sec. III-C,
+ * T_NN and the bounds of eq. tau_init / tau_min_nols) run in hac_batch_create;
+ * its search loop (construction by Algorithm 2, iteration best, global best
+ * with recomputed bounds, bounded evaporation/deposit of eq. pheromone_update)
+ * runs in hac_batch_iterate. */
 typedef struct hac_batch hac_batch;
 
 /* Bytes of device workspace needed by hac_batch_create for these instances.

@@ -260,7 +260,7 @@ typedef struct {
     orc_instance in;
     orc_params p;
     int n, k_eff, k_pad;
-    /* preparation (Alg. 1 lines 2-3) */
+    /* preparation (Algorithm 1) */
     int32_t *cand;      /* n*k_pad, -1 on pad slots, ascending (d, j) */
     double *cdist;      /* n*k_pad, d_ij of each slot */
     double *conf;       /* n*k_pad, thresholded confidence c_ij, eq. (confidence) */
@@ -272,7 +272,7 @@ typedef struct {
     double q90, Rhat, kappa, p_x;
     int32_t *nbr;       /* n*ls_k geometric lists for 2-opt */
     int ls_k;
-    /* initialisation (lines 4-6) */
+    /* initialisation */
     int32_t *nn_tour;
     double L_nn;
     double tau_max64, tau_min64;
@@ -360,7 +360,7 @@ double orc_quantile7(const double *x, int64_t N, double q)
 
 /* p_x = p_best^(1/n) and the dynamic range R = tau_max/tau_min of eq. (tau_init)
  * or eq. (tau_min_nols).  R does not involve L_nn, which is why kappa can be
- * set before the nearest-neighbour tour exists (Alg. 1 line 3 before line 5).
+ * set before the nearest-neighbour tour exists, as Algorithm 1 orders them.
  * Reading: the "k" of eq. (tau_min_nols) is the candidate-list size in use,
  * min(k, n-1). */
 static void dynamic_range(orc_state *S)
@@ -573,7 +573,7 @@ static int nearest_unvisited(const orc_instance *in, const uint8_t *vis, int i)
     return best;
 }
 
-/* Reading: T_NN starts at node 0 (Alg. 1 line 4 does not say where). */
+/* Reading: T_NN starts at node 0 (Algorithm 1 does not say where). */
 static void nn_tour(orc_state *S)
 {
     int n = S->n;
@@ -738,7 +738,7 @@ static void iterate_once(orc_state *S)
 {
     int n = S->n, m = S->p.m, kp = S->k_pad;
     for (int a = 0; a < m; ++a) construct(S, a, S->tours + (int64_t)a * n, &S->lens[a]);
-    if (S->p.local_search == 2)                          /* Alg. 1 line 10: 2-opt on every ant */
+    if (S->p.local_search == 2)                          /* Algorithm 1: local search on every ant */
         for (int a = 0; a < m; ++a) {
             orc_two_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
             S->lens[a] = orc_tour_length(&S->in, S->tours + (int64_t)a * n);
@@ -854,7 +854,7 @@ void orc_destroy(void *h)
     free(S);
 }
 
-/* Preparation and initialisation, Alg. 1 lines 1-6. */
+/* Preparation and initialisation of Algorithm 1. */
 void *orc_create(const orc_instance *in, const orc_params *p, int32_t *status)
 {
     int st = check_inputs(in, p);
@@ -891,25 +891,25 @@ void *orc_create(const orc_instance *in, const orc_params *p, int32_t *status)
         if (status) *status = ORC_ENOMEM;
         return NULL;
     }
-    build_candidates(S);                  /* line 2 */
-    build_evidence(S);                    /* line 3: e_ij, q90, kappa */
+    build_candidates(S);                  /* candidate lists */
+    build_evidence(S);                    /* e_ij, q90, kappa */
     build_weights(S);
     if (S->ls_k) build_nbr(S);
-    nn_tour(S);                           /* line 4 */
-    set_bounds(S, S->L_nn);               /* line 5 */
+    nn_tour(S);                           /* T_NN */
+    set_bounds(S, S->L_nn);               /* bounds from L_nn */
     for (size_t s = 0; s < slots; ++s) {
         int real = S->cand[s] >= 0;
         S->tau[s] = real ? S->tau_max : 0.0f;
         S->choice[s] = real ? choice_of(S, S->tau[s], S->W[s]) : 0.0f;
     }
-    memcpy(S->gb_tour, S->nn_tour, n * sizeof(int32_t));   /* line 6 */
+    memcpy(S->gb_tour, S->nn_tour, n * sizeof(int32_t));   /* T_gb = T_NN */
     S->L_gb = S->L_nn;
     S->L_rb = INFINITY;                   /* restart-best: none yet */
     S->u_gb = 25;
     return S;
 }
 
-/* Alg. 1 lines 8-21 for `iters` more iterations. */
+/* The search loop of Algorithm 1 for `iters` more iterations. */
 int orc_iterate(void *h, int32_t iters)
 {
     orc_state *S = h;

@@ -1,5 +1,5 @@
 // Persistent fused iteration kernel: one thread-block cluster per instance runs
-// whole MMAS iterations (Algorithm 1 lines 9-19) without leaving the GPU.
+// whole MMAS iterations (the search loop of Algorithm 1) without leaving the GPU.
 //
 // Per instance the candidate table C_i (uint16 ids, padding slots hold n) and
 // choice_info (FP32)
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
         }
         __syncthreads();
         fallback_distances(I, a_lo, a_hi);     // this CTA's ants only: no cluster barrier needed
-        if (I.local_search == 2) {             // Alg. 1 line 10: 2-opt on every ant, each warp its own
+        if (I.local_search == 2) {             // Algorithm 1's local search on every ant, each warp its own
             for (int a = a_first; a < min(a_first + APW, a_hi); ++a) {
                 int32_t *tour = I.tours + (size_t)a * n;
                 warp_two_opt(I, tour, ls_ant(I, a));

@@ -1,4 +1,4 @@
-// End-of-iteration steps (Algorithm 1 lines 12-19) as block-level device
+// End-of-iteration steps of Algorithm 1 as block-level device
 // functions, shared by the per-iteration kernels and the fused cluster kernel:
 //   iteration_best   T_ib = argmin over ants of L (ties to the lower ant), copied out
 //   global_best      restart-best T_rb (schedule = 1), new global best -> T_gb,

@@ -1,4 +1,5 @@
-// Preparation of every instance of a batch: Algorithm 1 lines 2-6.
+// Preparation of every instance of a batch: the preparation and initialisation
+// steps of Algorithm 1.
 //
 //   heatmap view    h = (H + H^T)/2 when symmetrised (Sec. II-B): column i of H
 //                   is materialised as a sorted row (counting transpose)

@@ -24,7 +24,7 @@ __global__ void k_two_opt_ib(const DevInst *insts, unsigned smem_bytes)
     if (threadIdx.x == 0) I.st->L_ib = L;
 }
 
-// local_search = 2 (Alg. 1 line 10): ant blockIdx.x % max_m of instance
+// local_search = 2 (Algorithm 1's local search on every ant): ant blockIdx.x % max_m of instance
 // blockIdx.x / max_m, right after construction; its length is recomputed
 __global__ void k_two_opt_all(const DevInst *insts, int max_m, unsigned smem_bytes)
 {

@@ -1,5 +1,5 @@
 // First-improvement 2-opt with geometric neighbour lists and don't-look bits
-// (Sec. III-D), one warp per instance, applied to T_NN once (Alg. 1 line 4)
+// (Sec. III-D), one warp per instance, applied to T_NN once (Algorithm 1's initialisation)
 // and to the iteration-best tour before it updates the pheromone.
 //
 // Order of the search (it defines the result):

@@ -269,7 +269,7 @@ def test_mmas_schedule_parity(hac, orc, ex):
         bt.close()
 
 
-# ------------------------------------------------------------------ 2-opt on every ant (Alg. 1 line 10)
+# ------------------------------------------------------------------ 2-opt on every ant (Algorithm 1's local search)
 
 @pytest.mark.parametrize("ex", [dict(apw=4, fused=1, clog=0), dict(apw=2, fused=1, clog=1),
                                 dict(apw=4, fused=0, clog=0), dict(apw=1, fused=0, clog=0)],

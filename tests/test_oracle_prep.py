@@ -1,6 +1,6 @@
 """Pins of the oracle's preparation: candidate lists (Sec. III-A), the evidence
 factor and its scale (Sec. III-C), the bounds (eqs. tau_init, tau_min_nols) and
-the nearest-neighbour tour (Alg. 1 line 4)."""
+the nearest-neighbour tour of Algorithm 1."""
 import math
 
 import numpy as np

@@ -295,7 +295,7 @@ def test_local_search_run_keeps_invariants(orc):
 
 
 def test_local_search_on_every_ant(orc):
-    # Alg. 1 line 10 with local_search = 2: every ant's tour is 2-opted before
+    # Algorithm 1's local search with local_search = 2: every ant's tour is 2-opted before
     # the iteration best is taken; lengths are those of the improved tours
     from paper_2601_19041_gb300 import synth
     inst = synth.euclid_instance(92, 150, K=10)
