@@ -688,13 +688,12 @@ static void construct(orc_state *S, int a, int32_t *T, double *Lout)
 
 /* --------------------------------------------- MMAS schedule (Alg. 1, III-B)
  *
- * Sec. III-B keeps the MMAS machinery: the elite tour T+ is the iteration-best
- * tour on most iterations and the restart-best tour every u_gb iterations,
- * u_gb tightening from 25 to 1 as the search goes on; every 100 iterations,
- * when the restart-best tour has not improved for more than 250 iterations and
- * the branching factor is below lambda_bf = 1 + 1e-5 (band fraction
- * xi_bf = 0.05, Sec. IV-D), the pheromone is reset to tau_max and the
- * restart-best tour is cleared; the global-best tour is kept.  The steps of
+ * What Sec. III-B and Sec. IV-D fix: which tour deposits alternates between
+ * T_ib and the restart-best T_rb, T_rb taking a growing share (its period
+ * u_gb shrinks from 25 to 1); a stagnation check runs every 100 iterations
+ * and, if T_rb is more than 250 iterations old and the branching factor
+ * (band 0.05) is under 1 + 1e-5, resets every trail to tau_max and forgets
+ * T_rb while T_gb survives.  The steps of
  * u_gb and the branching-factor normalisation are not printed in the paper;
  * the ones used here are the MMAS ones (Stuetzle and Hoos, 2000): u_gb = 25,
  * 5, 3, 2, 1 for s < 25, 75, 125, 250 and beyond, s = iterations since the
