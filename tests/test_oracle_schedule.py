@@ -2,13 +2,12 @@
 Algorithm 1): the u_gb elite schedule, the restart-best tour, the branching
 factor and the restarts.
 
-The paper fixes: u_gb tightens from 25 to 1; T+ is the iteration-best tour on
-most iterations and the restart-best one every u_gb iterations; every 100
-iterations, when the restart-best tour has not improved for more than 250
-iterations and the branching factor (band fraction 0.05) is below 1 + 1e-5,
-tau is reset to tau_max, T_rb is cleared and T_gb is kept.  The checks below
-derive each of these from the run's own trace and from pheromone matrices of
-known form."""
+The paper fixes: the depositing tour alternates between T_ib and T_rb with a
+period u_gb that shrinks from 25 to 1; a check every 100 iterations resets
+the trails to tau_max and forgets T_rb (keeping T_gb) when T_rb is more than
+250 iterations old and the branching factor (band 0.05) is under 1 + 1e-5.
+The checks below derive each of these from the run's own trace and from
+pheromone matrices of known form."""
 import numpy as np
 import pytest
 
