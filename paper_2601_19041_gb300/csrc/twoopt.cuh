@@ -22,11 +22,13 @@
 // out: el[p] holds d(tour[p], tour[p+1]) in FP32 and nbrd32 the neighbour
 // distances.  Each FP32 distance is within 4 units of 2^-24 (relative) of the
 // FP64 one, so the FP32 estimate of the four-term gain is within about
-// 8 * 2^-24 of the sum of the four magnitudes; a candidate is examined in
-// FP64 unless its estimate lies below 1e-10 by more than 4e-6 times that sum
-// (plus 1e-18 for FP32 underflow).  Likewise d(a, b) is compared with
-// d(a, dir a) in FP32 with a relative margin of 4e-6 before the exact test.
-// The moves taken are therefore exactly those of the plain FP64 search.
+// 8 * 2^-24 of the sum of the four magnitudes.  With tol = 4e-6 times that
+// sum (plus 1e-18 for FP32 underflow), an estimate below 1e-10 - tol means the
+// FP64 gain is certainly <= 1e-10, one above 1e-10 + tol that it is certainly
+// above; only estimates in between are decided in FP64.  Likewise d(a, b) is
+// compared with d(a, dir a) in FP32 with a relative margin of 4e-6 on either
+// side.  The moves taken are therefore exactly those of the plain FP64 search;
+// the FP32 edge lengths stored for the new edges are FP32 estimates too.
 //
 // Parallelism inside the sequential search: when more than LS_FEW of the
 // next 32 tour positions hold cities whose bit is clear, a pass examines them
@@ -66,12 +68,21 @@ __device__ __forceinline__ float ls_d32(const float2 *xy, int u, int v)
     return __fsqrt_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)));
 }
 
-// false only if the FP64 gain is certainly <= LS_GAIN
-__device__ __forceinline__ bool ls_may_improve(float da, float dab, float dbb, float dn)
+// the FP64 gain from FP32 estimates of its terms: 0 certainly <= LS_GAIN,
+// 2 certainly above, 1 undecided
+__device__ __forceinline__ int ls_gain_class(float da, float dab, float dbb, float dn)
 {
     const float est = __fsub_rn(__fadd_rn(__fsub_rn(da, dab), dbb), dn);
     const float mag = __fadd_rn(__fadd_rn(da, dab), __fadd_rn(dbb, dn));
-    return est > __fsub_rn((float)LS_GAIN, __fadd_rn(__fmul_rn(4e-6f, mag), 1e-18f));
+    const float tol = __fadd_rn(__fmul_rn(4e-6f, mag), 1e-18f);
+    if (!(est > __fsub_rn((float)LS_GAIN, tol))) return 0;
+    return est > __fadd_rn((float)LS_GAIN, tol) ? 2 : 1;
+}
+
+// false only if the FP64 gain is certainly <= LS_GAIN
+__device__ __forceinline__ bool ls_may_improve(float da, float dab, float dbb, float dn)
+{
+    return ls_gain_class(da, dab, dbb, dn) != 0;
 }
 
 // reverse so that (x, succ x), (y, succ y) become (x, y), (succ x, succ y);
@@ -90,25 +101,47 @@ __device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, in
         len += 1;
     }
     __syncwarp();
-    for (int t = lane; t < len / 2; t += 32) {
-        int p = i0 + t;
-        if (p >= n) p -= n;
-        int q = i0 + len - 1 - t;
-        if (q >= n) q -= n;
-        const int u = M.tour[p], v = M.tour[q];
-        M.tour[p] = v;
-        M.tour[q] = u;
-        M.pos[v] = p;
-        M.pos[u] = q;
+    // the pairs (p, q) of different t are disjoint, so each lane loads two
+    // pairs before it stores them
+    const int h = len / 2;
+    for (int t = lane; t < h; t += 64) {
+        const bool two = t + 32 < h;
+        int p0 = i0 + t, q0 = i0 + len - 1 - t;
+        int p1 = p0 + 32, q1 = q0 - 32;
+        if (p0 >= n) p0 -= n;
+        if (q0 >= n) q0 -= n;
+        if (p1 >= n) p1 -= n;
+        if (q1 >= n) q1 -= n;
+        const int u0 = M.tour[p0], v0 = M.tour[q0];
+        const int u1 = two ? M.tour[p1] : 0, v1 = two ? M.tour[q1] : 0;
+        M.tour[p0] = v0;
+        M.tour[q0] = u0;
+        M.pos[v0] = p0;
+        M.pos[u0] = q0;
+        if (two) {
+            M.tour[p1] = v1;
+            M.tour[q1] = u1;
+            M.pos[v1] = p1;
+            M.pos[u1] = q1;
+        }
     }
-    for (int t = lane; t < (len - 1) / 2; t += 32) {
-        int p = i0 + t;
-        if (p >= n) p -= n;
-        int q = i0 + len - 2 - t;
-        if (q >= n) q -= n;
-        const float u = M.el[p], v = M.el[q];
-        M.el[p] = v;
-        M.el[q] = u;
+    const int he = (len - 1) / 2;
+    for (int t = lane; t < he; t += 64) {
+        const bool two = t + 32 < he;
+        int p0 = i0 + t, q0 = i0 + len - 2 - t;
+        int p1 = p0 + 32, q1 = q0 - 32;
+        if (p0 >= n) p0 -= n;
+        if (q0 >= n) q0 -= n;
+        if (p1 >= n) p1 -= n;
+        if (q1 >= n) q1 -= n;
+        const float u0 = M.el[p0], v0 = M.el[q0];
+        const float u1 = two ? M.el[p1] : 0.0f, v1 = two ? M.el[q1] : 0.0f;
+        M.el[p0] = v0;
+        M.el[q0] = u0;
+        if (two) {
+            M.el[p1] = v1;
+            M.el[q1] = u1;
+        }
     }
     __syncwarp();
     if (lane == 0) {
@@ -120,36 +153,42 @@ __device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, in
     __syncwarp();
 }
 
-// FP32 test of one city by one lane: could some move of it improve?
-__device__ __forceinline__ bool ls_city_may_move(const DevInst &I, const LsMem &M, int n, int K, int a)
+// FP32 test of one city a at position pa by one lane: could some move of it
+// improve?  Four neighbours at a time, both directions at once: every load is
+// of a valid city or position, so they all issue together and only the
+// results are masked.
+__device__ __forceinline__ bool ls_city_may_move(const DevInst &I, const LsMem &M, int n, int K, int a, int pa)
 {
     const int32_t *nb = I.nbr + (size_t)a * K;
     const float *nd = I.nbrd32 + (size_t)a * K;
-    const int pa = M.pos[a];
-    for (int dir = 0; dir < 2; ++dir) {
-        const int an = dir == 0 ? M.tour[wrap_next(pa, n)] : M.tour[wrap_prev(pa, n)];
-        const float da = M.el[dir == 0 ? pa : wrap_prev(pa, n)];
-        for (int k0 = 0; k0 < K; k0 += 4) {
-            // four neighbours' entries at once (independent loads), then in order
-            float dab4[4];
-            int b4[4];
+    const int pv = wrap_prev(pa, n);
+    const int an0 = M.tour[wrap_next(pa, n)], an1 = M.tour[pv];
+    const float da0 = M.el[pa], da1 = M.el[pv];
+    for (int k0 = 0; k0 < K; k0 += 4) {
+        float dab[4];
+        int b[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                dab4[q] = k0 + q < K ? nd[k0 + q] : __int_as_float(0x7f800000);
-                b4[q] = k0 + q < K ? nb[k0 + q] : 0;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!(da > __fmul_rn(dab4[q], LS_G1_LO))) goto next_dir;   // the list ascends: no later b either
-                const int b = b4[q];
-                const int pb = M.pos[b];
-                const int bn = dir == 0 ? M.tour[wrap_next(pb, n)] : M.tour[wrap_prev(pb, n)];
-                if (b == an || bn == a) continue;
-                const float dbb = M.el[dir == 0 ? pb : wrap_prev(pb, n)];
-                if (ls_may_improve(da, dab4[q], dbb, ls_d32(M.xy, an, bn))) return true;
-            }
+        for (int q = 0; q < 4; ++q) {
+            dab[q] = k0 + q < K ? nd[k0 + q] : __int_as_float(0x7f800000);
+            b[q] = k0 + q < K ? nb[k0 + q] : 0;
         }
-    next_dir:;
+        bool hit = false;
+        bool v0 = false, v1 = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // the list ascends: once d(a, b) reaches d(a, dir a), no later b either
+            const float lim = __fmul_rn(dab[q], LS_G1_LO);
+            v0 = da0 > lim;
+            v1 = da1 > lim;
+            const int pb = M.pos[b[q]];
+            const int pbv = wrap_prev(pb, n);
+            const int bn0 = M.tour[wrap_next(pb, n)], bn1 = M.tour[pbv];
+            const float dbb0 = M.el[pb], dbb1 = M.el[pbv];
+            hit |= v0 && b[q] != an0 && bn0 != a && ls_may_improve(da0, dab[q], dbb0, ls_d32(M.xy, an0, bn0));
+            hit |= v1 && b[q] != an1 && bn1 != a && ls_may_improve(da1, dab[q], dbb1, ls_d32(M.xy, an1, bn1));
+        }
+        if (hit) return true;
+        if (!(v0 || v1)) return false;
     }
     return false;
 }
@@ -164,36 +203,43 @@ __device__ __forceinline__ bool ls_find_move(const DevInst &I, const LsMem &M, i
     const int pa = M.pos[a];
     an = dir == 0 ? M.tour[wrap_next(pa, n)] : M.tour[wrap_prev(pa, n)];
     const float da32 = M.el[dir == 0 ? pa : wrap_prev(pa, n)];
-    bool cand = false;
+    bool cand = false, sure = false;
     int bb = 0, bbn = 0;
+    float dnn = 0.0f;
     if (lane < K && da32 > __fmul_rn(nd32, LS_G1_LO)) {
         bb = nb;
         const int pb = M.pos[bb];
         bbn = dir == 0 ? M.tour[wrap_next(pb, n)] : M.tour[wrap_prev(pb, n)];
         if (!(bb == an || bbn == a)) {
             const float dbb = M.el[dir == 0 ? pb : wrap_prev(pb, n)];
-            cand = ls_may_improve(da32, nd32, dbb, ls_d32(M.xy, an, bbn));
+            dnn = ls_d32(M.xy, an, bbn);
+            const int g = ls_gain_class(da32, nd32, dbb, dnn);
+            cand = g != 0;
+            sure = g == 2 && __fmul_rn(da32, LS_G1_LO) > nd32;   // and d(a, b) < d(a, dir a) for certain
         }
     }
-    if (!__ballot_sync(FULL2, cand)) return false;
-    const double da = dist64(I, a, an);
-    bool ok = false;
-    double dnn = 0.0;
-    if (cand) {
-        const double g1 = __dsub_rn(da, nd64);
-        if (g1 > 0.0) {
-            dnn = dist64(I, an, bbn);
-            const double gain = __dsub_rn(__dadd_rn(g1, dist64(I, bb, bbn)), dnn);
-            ok = gain > LS_GAIN;
+    const unsigned cm = __ballot_sync(FULL2, cand);
+    if (!cm) return false;
+    int src = __ffs(cm) - 1;
+    if (!((__ballot_sync(FULL2, sure) >> src) & 1u)) {
+        // the first candidate is undecided in FP32: decide all of them in FP64
+        const double da = dist64(I, a, an);
+        bool ok = false;
+        if (cand) {
+            const double g1 = __dsub_rn(da, nd64);
+            if (g1 > 0.0) {
+                const double gain = __dsub_rn(__dadd_rn(g1, dist64(I, bb, bbn)), dist64(I, an, bbn));
+                ok = gain > LS_GAIN;
+            }
         }
+        const unsigned om = __ballot_sync(FULL2, ok);
+        if (!om) return false;
+        src = __ffs(om) - 1;
     }
-    const unsigned om = __ballot_sync(FULL2, ok);
-    if (!om) return false;
-    const int src = __ffs(om) - 1;
     b = __shfl_sync(FULL2, bb, src);
     bn = __shfl_sync(FULL2, bbn, src);
     dab = __shfl_sync(FULL2, nd32, src);
-    dn = __double2float_rn(__shfl_sync(FULL2, dnn, src));
+    dn = __shfl_sync(FULL2, dnn, src);
     return true;
 }
 
@@ -230,7 +276,7 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
                     p += __ffs(cm) - 1;     // few clear cities: the warp examines the first one
                 } else {
                     // many: the next 32 positions at once, one city per lane, FP32 test only
-                    const bool flag = clear && ls_city_may_move(I, M, n, K, al);
+                    const bool flag = clear && ls_city_may_move(I, M, n, K, al, pp);
                     const unsigned fm = __ballot_sync(FULL2, flag);
                     const int f = fm ? __ffs(fm) - 1 : 32;
                     if (clear && lane < f) M.dlb[al] = 1;   // examined, no move
