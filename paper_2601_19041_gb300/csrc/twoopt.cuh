@@ -31,11 +31,11 @@
 // the FP32 edge lengths stored for the new edges are FP32 estimates too.
 //
 // Parallelism inside the sequential search: when more than LS_FEW of the
-// next 32 tour positions hold cities whose bit is clear, a pass examines them
-// at once, one city per lane, with the FP32 test only; the cities before the
-// first one that might move have no move and get their bit at once (as they
-// would one by one, since examining a city without a move changes nothing
-// else).  A city that might move, or the first clear one when few are clear,
+// next 32 tour positions hold cities whose bit is clear, a pass tests them at
+// once with the FP32 test only, their candidate moves spread over the lanes;
+// the cities before the first one that might move have no move and get their
+// bit at once (as they would one by one, since examining a city without a move
+// changes nothing else).  A city that might move, or the first clear one when few are clear,
 // is examined by the whole warp, one neighbour per lane (FP32 test, then FP64
 // for the candidates that pass it).  Segment reversals swap element pairs
 // across lanes.
@@ -153,44 +153,77 @@ __device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, in
     __syncwarp();
 }
 
-// FP32 test of one city a at position pa by one lane: could some move of it
-// improve?  Four neighbours at a time, both directions at once: every load is
-// of a valid city or position, so they all issue together and only the
-// results are masked.
-__device__ __forceinline__ bool ls_city_may_move(const DevInst &I, const LsMem &M, int n, int K, int a, int pa)
+// FP32 pre-test of the clear cities of 32 consecutive positions (lane l holds
+// the city al at position pp = p + l): the lane of the first city that might
+// move, or 32.  A work item is one candidate move of one city: a direction and
+// a neighbour b while d(a, b) is below d(a, dir a) (FP32, with the margin);
+// the list ascends, so each direction's items are a prefix of the list.  The
+// items of all cities are dealt to the lanes in position order, 32 at a time;
+// after the first group with a possible move every earlier city has been
+// tested in full, so the search stops there.
+__device__ __forceinline__ int ls_first_may_move(const DevInst &I, const LsMem &M, int n, int K, bool clear, int al,
+                                                 int pp)
 {
-    const int32_t *nb = I.nbr + (size_t)a * K;
-    const float *nd = I.nbrd32 + (size_t)a * K;
-    const int pv = wrap_prev(pa, n);
-    const int an0 = M.tour[wrap_next(pa, n)], an1 = M.tour[pv];
-    const float da0 = M.el[pa], da1 = M.el[pv];
-    for (int k0 = 0; k0 < K; k0 += 4) {
-        float dab[4];
-        int b[4];
+    const int lane = threadIdx.x & 31;
+    int an0 = 0, an1 = 0, c0 = 0, c1 = 0;
+    float da0 = 0.0f, da1 = 0.0f;
+    if (clear) {
+        const int pv = wrap_prev(pp, n);
+        an0 = M.tour[wrap_next(pp, n)];
+        an1 = M.tour[pv];
+        da0 = M.el[pp];
+        da1 = M.el[pv];
+        const float *nd = I.nbrd32 + (size_t)al * K;
+        for (int k0 = 0; k0 < K; k0 += 4) {
+            float lim[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            dab[q] = k0 + q < K ? nd[k0 + q] : __int_as_float(0x7f800000);
-            b[q] = k0 + q < K ? nb[k0 + q] : 0;
-        }
-        bool hit = false;
-        bool v0 = false, v1 = false;
+            for (int q = 0; q < 4; ++q)
+                lim[q] = k0 + q < K ? __fmul_rn(nd[k0 + q], LS_G1_LO) : __int_as_float(0x7f800000);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            // the list ascends: once d(a, b) reaches d(a, dir a), no later b either
-            const float lim = __fmul_rn(dab[q], LS_G1_LO);
-            v0 = da0 > lim;
-            v1 = da1 > lim;
-            const int pb = M.pos[b[q]];
-            const int pbv = wrap_prev(pb, n);
-            const int bn0 = M.tour[wrap_next(pb, n)], bn1 = M.tour[pbv];
-            const float dbb0 = M.el[pb], dbb1 = M.el[pbv];
-            hit |= v0 && b[q] != an0 && bn0 != a && ls_may_improve(da0, dab[q], dbb0, ls_d32(M.xy, an0, bn0));
-            hit |= v1 && b[q] != an1 && bn1 != a && ls_may_improve(da1, dab[q], dbb1, ls_d32(M.xy, an1, bn1));
+            for (int q = 0; q < 4; ++q) {
+                c0 += da0 > lim[q];
+                c1 += da1 > lim[q];
+            }
+            if (!(da0 > lim[3] || da1 > lim[3])) break;
         }
-        if (hit) return true;
-        if (!(v0 || v1)) return false;
     }
-    return false;
+    const int cnt = c0 + c1;
+    int incl = cnt;     // inclusive prefix sum of the item counts over the lanes
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int v = __shfl_up_sync(FULL2, incl, s);
+        if (lane >= s) incl += v;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(FULL2, incl, 31);
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
+        int c = 0;      // the lane whose city owns item t: the number of lanes with incl <= t
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1)
+            if (__shfl_sync(FULL2, incl, c + s - 1) <= t) c += s;
+        const int j = t - __shfl_sync(FULL2, excl, c);
+        const int cc0 = __shfl_sync(FULL2, c0, c);
+        const int a = __shfl_sync(FULL2, al, c);
+        const int xan0 = __shfl_sync(FULL2, an0, c), xan1 = __shfl_sync(FULL2, an1, c);
+        const float xda0 = __shfl_sync(FULL2, da0, c), xda1 = __shfl_sync(FULL2, da1, c);
+        bool hit = false;
+        if (t < total) {
+            const int dir = j < cc0 ? 0 : 1;
+            const int q = dir == 0 ? j : j - cc0;
+            const int an = dir == 0 ? xan0 : xan1;
+            const float da = dir == 0 ? xda0 : xda1;
+            const int b = I.nbr[(size_t)a * K + q];
+            const float dab = I.nbrd32[(size_t)a * K + q];
+            const int pb = M.pos[b];
+            const int pe = dir == 0 ? pb : wrap_prev(pb, n);     // the edge (b, dir b)
+            const int bn = M.tour[dir == 0 ? wrap_next(pb, n) : pe];
+            if (b != an && bn != a) hit = ls_may_improve(da, dab, M.el[pe], ls_d32(M.xy, an, bn));
+        }
+        const unsigned first = __reduce_min_sync(FULL2, hit ? (unsigned)c : 32u);
+        if (first < 32u) return (int)first;
+    }
+    return 32;
 }
 
 // One direction of city a, one neighbour per lane: the first improving move
@@ -275,13 +308,11 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
                 if (__popc(cm) <= LS_FEW) {
                     p += __ffs(cm) - 1;     // few clear cities: the warp examines the first one
                 } else {
-                    // many: the next 32 positions at once, one city per lane, FP32 test only
-                    const bool flag = clear && ls_city_may_move(I, M, n, K, al, pp);
-                    const unsigned fm = __ballot_sync(FULL2, flag);
-                    const int f = fm ? __ffs(fm) - 1 : 32;
+                    // many: the next 32 positions at once, FP32 test only
+                    const int f = ls_first_may_move(I, M, n, K, clear, al, pp);
                     if (clear && lane < f) M.dlb[al] = 1;   // examined, no move
                     __syncwarp();
-                    if (!fm) { p += 32; continue; }
+                    if (f == 32) { p += 32; continue; }
                     p += f;
                 }
                 const int a = M.tour[p];
