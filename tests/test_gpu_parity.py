@@ -100,6 +100,14 @@ CASES = {
     "duplicate_points": lambda: (euclid(np.repeat(_pts(22, 40), 2, axis=0)), params(m=6, k=8, iterations=5, rho=0.2, seed=16)),
     "atsp": lambda: (synth.atsp_instance(23, 200, K=30), params(m=10, k=20, iterations=8, rho=0.2, degree_target=1, seed=17)),
     "two_opt": lambda: (synth.euclid_instance(24, 350, K=10), params(m=10, k=10, iterations=6, rho=0.2, local_search=1, seed=18)),
+    # an exact 17 x 17 grid: equal edge lengths make many gains exactly zero, which
+    # the FP32 estimate cannot decide and the FP64 test does; an odd list length
+    # leaves a partial group of four
+    "two_opt_grid": lambda: (euclid(np.stack(np.meshgrid(np.arange(17), np.arange(17)), -1).reshape(-1, 2) / 16.0),
+                             params(m=10, k=10, iterations=6, rho=0.2, local_search=1, ls_k=7, seed=23)),
+    # zero-length edges and the longest neighbour list
+    "two_opt_dup": lambda: (euclid(np.repeat(_pts(28, 45), 2, axis=0)),
+                            params(m=8, k=8, iterations=5, rho=0.2, local_search=1, ls_k=32, seed=24)),
     "clustered": lambda: (synth.euclid_instance(25, 300, K=50, family="gmm"), params(m=12, k=20, iterations=6, rho=0.2, seed=19)),
     "grid": lambda: (synth.euclid_instance(26, 289, K=50, family="grid"), params(m=12, k=20, iterations=6, rho=0.2, seed=20)),
 }
@@ -125,7 +133,7 @@ FUSED = [dict(apw=2, clog=0, fbl=32), dict(apw=4, clog=1, fbl=0), dict(apw=4, cl
 
 @pytest.mark.parametrize("cfg", FUSED, ids=lambda c: f"apw{c['apw']}_C{1 << c['clog']}_fbl{c['fbl']}")
 @pytest.mark.parametrize("name", ["sym50nn_k20", "sym10nn_k10_ragged", "k32", "k7_pad", "n3",
-                                  "empty_heatmap", "atsp", "two_opt", "alpha_beta_powers"])
+                                  "empty_heatmap", "atsp", "two_opt", "two_opt_grid", "alpha_beta_powers"])
 def test_fused_kernel_parity(hac, orc, name, cfg):
     inst, p = CASES[name]()
     ex = hac.make_exec(cfg["apw"], 0, 1, fused=1, fallback_list=cfg["fbl"], cluster_log2=cfg["clog"])
