@@ -50,6 +50,13 @@ constexpr float LS_G1_LO = 0.999996f;   // d(a,dir a) <= this * d(a,b) in FP32: 
 constexpr int LS_FEW = 4;               // at most this many clear cities in 32 positions: one at a time
 
 __device__ __forceinline__ int wrap_next(int p, int n) { return p + 1 < n ? p + 1 : 0; }
+
+// bring the cache lines of a row of `bytes` bytes into L1 (no fault, no result)
+__device__ __forceinline__ void ls_prefetch_row(const void *row, int bytes)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(row));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(static_cast<const char *>(row) + bytes - 1));
+}
 __device__ __forceinline__ int wrap_prev(int p, int n) { return p > 0 ? p - 1 : n - 1; }
 
 // the arrays of one search: shared memory (a kernel of its own) or the workspace
@@ -173,6 +180,7 @@ __device__ __forceinline__ int ls_first_may_move(const DevInst &I, const LsMem &
         an1 = M.tour[pv];
         da0 = M.el[pp];
         da1 = M.el[pv];
+        ls_prefetch_row(I.nbr + (size_t)al * K, K * 4);      // read by the work items below
         const float *nd = I.nbrd32 + (size_t)al * K;
         for (int k0 = 0; k0 < K; k0 += 4) {
             float lim[4];
@@ -308,7 +316,13 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
                 if (__popc(cm) <= LS_FEW) {
                     p += __ffs(cm) - 1;     // few clear cities: the warp examines the first one
                 } else {
-                    // many: the next 32 positions at once, FP32 test only
+                    // many: the next 32 positions at once, FP32 test only; the
+                    // lists of the 32 positions after them are warmed for the next test
+                    if (pp + 32 < n) {
+                        const int ah = M.tour[pp + 32];
+                        ls_prefetch_row(I.nbrd32 + (size_t)ah * K, K * 4);
+                        ls_prefetch_row(I.nbr + (size_t)ah * K, K * 4);
+                    }
                     const int f = ls_first_may_move(I, M, n, K, clear, al, pp);
                     if (clear && lane < f) M.dlb[al] = 1;   // examined, no move
                     __syncwarp();
