@@ -17,10 +17,10 @@
 //   that strictly decreasing tour lengths never reach in practice), so the
 //   kernel always terminates.
 //
-// Every move is decided in FP64 (d_ij as in the length, gain = (d(a,dir a) -
-// d(a,b)) + d(b,dir b) - d(dir a,dir b)).  FP32 copies only rule candidates
-// out: el[p] holds d(tour[p], tour[p+1]) in FP32 and nbrd32 the neighbour
-// distances.  Each FP32 distance is within 4 units of 2^-24 (relative) of the
+// Moves follow the FP64 gain (d_ij as in the length, gain = (d(a,dir a) -
+// d(a,b)) + d(b,dir b) - d(dir a,dir b)), but most candidates are decided from
+// FP32 copies: el[p] holds d(tour[p], tour[p+1]) in FP32 and nbrd32 the
+// neighbour distances.  Each FP32 distance is within 4 units of 2^-24 (relative) of the
 // FP64 one, so the FP32 estimate of the four-term gain is within about
 // 8 * 2^-24 of the sum of the four magnitudes.  With tol = 4e-6 times that
 // sum (plus 1e-18 for FP32 underflow), an estimate below 1e-10 - tol means the
@@ -35,10 +35,10 @@
 // once with the FP32 test only, their candidate moves spread over the lanes;
 // the cities before the first one that might move have no move and get their
 // bit at once (as they would one by one, since examining a city without a move
-// changes nothing else).  A city that might move, or the first clear one when few are clear,
-// is examined by the whole warp, one neighbour per lane (FP32 test, then FP64
-// for the candidates that pass it).  Segment reversals swap element pairs
-// across lanes.
+// changes nothing else).  A city that might move, or the first clear one when
+// few are clear, is examined by the whole warp, one neighbour per lane (FP32
+// classes, then FP64 when the first candidate is undecided).  Segment
+// reversals swap element pairs across lanes.
 #pragma once
 
 #include "lengths.cuh"
@@ -46,18 +46,18 @@
 namespace hac {
 
 constexpr unsigned FULL2 = 0xffffffffu;
-constexpr float LS_G1_LO = 0.999996f;   // d(a,dir a) <= this * d(a,b) in FP32: g1 < 0 in FP64
+constexpr float LS_G1_LO = 0.999996f;   // FP32 margin between d(a,b) and d(a,dir a): g1 <= 0 or > 0 for certain
 constexpr int LS_FEW = 4;               // at most this many clear cities in 32 positions: one at a time
 
 __device__ __forceinline__ int wrap_next(int p, int n) { return p + 1 < n ? p + 1 : 0; }
+__device__ __forceinline__ int wrap_prev(int p, int n) { return p > 0 ? p - 1 : n - 1; }
 
-// bring the cache lines of a row of `bytes` bytes into L1 (no fault, no result)
+// bring the cache lines of a global row of `bytes` bytes into L1 (no result)
 __device__ __forceinline__ void ls_prefetch_row(const void *row, int bytes)
 {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(row));
     asm volatile("prefetch.global.L1 [%0];" ::"l"(static_cast<const char *>(row) + bytes - 1));
 }
-__device__ __forceinline__ int wrap_prev(int p, int n) { return p > 0 ? p - 1 : n - 1; }
 
 // the arrays of one search: shared memory (a kernel of its own) or the workspace
 struct LsMem {
