@@ -205,3 +205,154 @@ def test_rejects_bad_inputs(orc):
     H = np.zeros((5, 5)); H[0, 1] = 1.5
     with pytest.raises(ValueError):
         orc.Oracle(euclid(pts, H), params(m=3, k=4, rho=0.2))
+
+
+# ---------------------------------------------------------------------------
+# The static weight W = fl32(eta^beta * exp(min(kappa * ln e, clip))) of the end
+# of Sec. III-C and eq. (transition), and choice = fl32(tau^alpha * W), checked
+# against an independent high-precision evaluation (mpmath) of the same
+# definition.  The oracle's FP64 pre-rounding value carries a relative error of
+# a few 1e-15 (own exp/ln within 2 ulp, a handful of roundings); a float32
+# rounding decision can only depend on it when the exact value lies within
+# 1e-12 (relative) of a float32 rounding midpoint, and such slots are counted
+# and skipped (there are none in practice).
+
+_MID_TOL = 1e-12
+
+
+def _fl32_of_exact(x, mpmath):
+    """float32 nearest to the mpmath value x > 0, or None when x is within
+    _MID_TOL of a float32 rounding midpoint (decision not pinned)."""
+    f = np.float32(float(x))                       # a float32 next to x
+    lo = f if mpmath.mpf(float(f)) <= x else np.nextafter(f, np.float32(0))
+    hi = np.nextafter(lo, np.float32(np.inf))
+    mid = (mpmath.mpf(float(lo)) + mpmath.mpf(float(hi))) / 2
+    if abs(x - mid) <= _MID_TOL * x:
+        return None
+    return lo if x < mid else hi
+
+
+def _exact_weights(o, p, mpmath, kappa=None):
+    """W of every real slot from the definition, in 60-digit arithmetic, from the
+    oracle's FP64 inputs d_ij, c_ij and b_i (pinned by the tests above) and its
+    kappa (pinned by the cap identity)."""
+    mpmath.mp.dps = 60
+    kap = mpmath.mpf(o.scalars()["kappa"] if kappa is None else kappa)
+    cdist, conf, base = o.get("cdist"), o.get("conf"), o.get("base")
+    clip, eps, beta = mpmath.mpf(p.logw_clip), mpmath.mpf(p.eps), mpmath.mpf(p.beta)
+    out = {}
+    for i in range(o.n):
+        b = mpmath.mpf(float(base[i]))
+        for c in range(o.k_eff):
+            d = max(float(cdist[i, c]), 1e-9)
+            eta = 1 / mpmath.mpf(d)
+            e = max(max(mpmath.mpf(float(conf[i, c])), eps) / b, mpmath.mpf(1))
+            lw = kap * mpmath.log(e) if e > 1 else mpmath.mpf(0)
+            out[(i, c)] = mpmath.power(eta, beta) * mpmath.exp(min(lw, clip))
+    return out
+
+
+def _check_weights(o, p, mpmath, kappa=None):
+    exact = _exact_weights(o, p, mpmath, kappa)
+    W = o.get("W")
+    skipped = 0
+    for (i, c), x in exact.items():
+        ref = _fl32_of_exact(x, mpmath)
+        if ref is None:
+            skipped += 1
+            continue
+        assert W[i, c] == ref, (i, c, float(W[i, c]), float(x))
+    assert skipped <= max(1, len(exact) // 1000)
+    assert np.all(W[:, o.k_eff:] == 0.0)
+    return exact
+
+
+def test_weights_with_evidence_match_exact_evaluation(orc):
+    """kappa > 0 on the n=500 workload instance: every W equals the float32
+    rounding of the exactly evaluated eta^2 * e^kappa.  A dropped or halved
+    exponent, a wrong eta power or a misplaced clip changes most slots."""
+    mpmath = pytest.importorskip("mpmath")
+    inst, ps = synth.workload("tsp500")
+    p = ps[0]
+    p.iterations = 0
+    o = orc.Oracle(inst[0], p)
+    s = o.scalars()
+    assert s["kappa"] > 0.5 and s["n_lambda"] >= 900           # evidence is active (top 2 per row)
+    logev = o.get("logev")
+    assert (s["kappa"] * logev).max() > 2.0                   # factors well above 1
+    exact = _check_weights(o, p, mpmath)
+    # the evidence really enters: W differs from eta^2 on every slot with e > 1
+    D = o.get("cdist")
+    eta2 = (1.0 / D[:, :o.k_eff]) ** 2
+    W = o.get("W")[:, :o.k_eff]
+    on = logev[:, :o.k_eff] > 0
+    assert np.all(W[on] > eta2[on].astype(np.float32) * 1.0001)
+    assert len(exact) == 500 * 20
+
+
+def test_weight_clip_fires(orc):
+    """A log-weight clip below kappa*ln(e) caps the factor at exp(clip)
+    (end of Sec. III-C): W = fl32(eta^2 * exp(clip)) on the clipped slots."""
+    mpmath = pytest.importorskip("mpmath")
+    inst, ps = synth.workload("tsp500")
+    p = ps[0]
+    p.iterations, p.logw_clip = 0, 1.25
+    o = orc.Oracle(inst[0], p)
+    kl = o.scalars()["kappa"] * o.get("logev")
+    clipped = kl > 1.25
+    assert 50 < clipped.sum() < kl.size - 50                   # both sides occur
+    _check_weights(o, p, mpmath)
+    D = o.get("cdist")
+    for i, c in zip(*np.nonzero(clipped)):
+        x = (1 / mpmath.mpf(float(D[i, c]))) ** 2 * mpmath.exp(mpmath.mpf(1.25))
+        ref = _fl32_of_exact(x, mpmath)
+        if ref is not None:
+            assert o.get("W")[i, c] == ref
+
+
+def test_hand_worked_weight_row(orc):
+    """Row 0 of the 6-node line: e = 5, 3, 1, 1, 1 over candidates at
+    distances 1/8 .. 5/8, so W_0c = 64/c^2 * e_c^kappa."""
+    mpmath = pytest.importorskip("mpmath")
+    pts, H = _hand_instance()
+    p = params(m=2, k=8, iterations=0, rho=0.2)
+    o = orc.Oracle(euclid(pts, H, symmetrize=0), p)
+    kap = o.scalars()["kappa"]
+    assert kap > 0
+    W = o.get("W")[0]
+    for c, e in enumerate([5, 3, 1, 1, 1]):
+        x = mpmath.mpf(64) / (c + 1) ** 2 * mpmath.power(e, mpmath.mpf(kap))
+        assert W[c] == _fl32_of_exact(x, mpmath)
+
+
+def test_weights_beta_three(orc):
+    """beta != 2 takes eta^beta = exp(beta ln eta) with the oracle's own exp/ln."""
+    mpmath = pytest.importorskip("mpmath")
+    inst, ps = synth.workload("tsp500")
+    p = ps[0]
+    p.iterations, p.beta = 0, 3.0
+    o = orc.Oracle(inst[0], p)
+    _check_weights(o, p, mpmath)
+
+
+def test_choice_alpha_power(orc):
+    """choice = fl32(tau^alpha * W) (numerator of eq. transition) for alpha=1.5
+    after some iterations, against the exact power of the stored tau and W."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    inst, ps = synth.workload("tsp500")
+    p = ps[0]
+    p.iterations, p.alpha, p.m = 3, 1.5, 8
+    o = orc.Oracle(inst[0], p).iterate(3)
+    tau, W, ch = o.get("tau"), o.get("W"), o.get("choice")
+    assert len(np.unique(tau[:, :20])) > 3                    # several pheromone levels
+    skipped = 0
+    for i in range(0, 500, 7):
+        for c in range(20):
+            x = mpmath.power(mpmath.mpf(float(tau[i, c])), mpmath.mpf(1.5)) * mpmath.mpf(float(W[i, c]))
+            ref = _fl32_of_exact(x, mpmath)
+            if ref is None:
+                skipped += 1
+                continue
+            assert ch[i, c] == ref, (i, c)
+    assert skipped <= 2
