@@ -53,6 +53,7 @@ typedef struct {
     int32_t baseline_scope;  /* 0 order statistic over C_i, 1 over the whole heatmap row */
     int32_t ls_k;            /* geometric neighbour-list size of the 2-opt */
     int32_t schedule;        /* 0: T+ = T_ib always; 1: MMAS u_gb schedule and restarts */
+    int32_t kappa_mode;      /* 0: eq. (kappa); 1: fixed kappa = 1; 2: eq. (kappa) without c_cap */
     uint64_t seed;
 } orc_params;
 
@@ -269,6 +270,7 @@ typedef struct {
     double *logev;      /* n*k_pad, ln e_ij (0 where e_ij = 1) */
     float *W;           /* n*k_pad, fl32(eta^beta * e^kappa) */
     int64_t n_lambda;
+    int64_t n_edges;    /* |E_theta(h)| = sum_i |P_i|, directed entries above theta_h (Sec. VI-A) */
     double q90, Rhat, kappa, p_x;
     int32_t *nbr;       /* n*ls_k geometric lists for 2-opt */
     int ls_k;
@@ -318,6 +320,7 @@ static void build_candidates(orc_state *S)
             dj_pair q = {orc_dist(in, i, j), j};
             if (orc_heat(in, i, j) > S->p.theta_h) mem[nm++] = q; else non[nn++] = q;
         }
+        S->n_edges += nm;
         qsort(mem, (size_t)nm, sizeof *mem, cmp_dj);
         dj_pair list[ORC_KMAX];
         int c = 0;
@@ -408,8 +411,14 @@ static void build_evidence(orc_state *S)
     S->n_lambda = N;
     S->q90 = orc_quantile7(lam, N, S->p.q_level);   /* eq. (q90) */
     dynamic_range(S);                                /* eq. (tau_ratio) */
-    if (S->q90 > 0.0 && S->Rhat > 1.0)               /* eq. (kappa) */
-        S->kappa = ((S->p.c_cap * S->p.alpha) * orc_ln(S->Rhat)) / S->q90;
+    /* eq. (kappa), and the two ablation variants of Sec. V-D: "fixed kappa = 1"
+     * drops the instance-level scale altogether; "no cap" keeps the scale by
+     * q90 and the pheromone range but drops the cap factor c_cap (reading:
+     * the paper prints no formula for this variant). */
+    if (S->p.kappa_mode == 1)
+        S->kappa = 1.0;
+    else if (S->q90 > 0.0 && S->Rhat > 1.0)
+        S->kappa = ((S->p.kappa_mode == 2 ? S->p.alpha : S->p.c_cap * S->p.alpha) * orc_ln(S->Rhat)) / S->q90;
     else
         S->kappa = 0.0;
     free(pos); free(lam);
@@ -836,8 +845,14 @@ static int check_inputs(const orc_instance *in, const orc_params *p)
     }
     if (p->rho <= 0.0 || p->rho >= 1.0 || p->degree_target < 1) return ORC_EINVAL;
     if (p->schedule != 0 && p->schedule != 1) return ORC_EINVAL;
+    if (p->kappa_mode < 0 || p->kappa_mode > 2) return ORC_EINVAL;
     if (p->local_search < 0 || p->local_search > 2) return ORC_EINVAL;
     if (p->local_search && (in->kind != 0 || p->ls_k < 1 || p->ls_k > in->n - 1)) return ORC_EINVAL;
+    /* the 2-opt's FP32 pre-test needs finite squared coordinate differences:
+     * |x|, |y| <= 1e18 with local search (the CUDA path checks the same) */
+    if (p->local_search)
+        for (int64_t q = 0; q < 2 * (int64_t)in->n; ++q)
+            if (!(fabs((double)in->coords[q]) <= 1e18)) return ORC_EINVAL;
     return ORC_OK;
 }
 
@@ -932,7 +947,7 @@ int orc_get(void *h, int32_t field, void *dst, int64_t bytes)
     size_t n = (size_t)S->n, slots = n * (size_t)S->k_pad, m = (size_t)S->p.m;
     const void *src = NULL;
     size_t sz = 0;
-    double scal[13];
+    double scal[14];
     int64_t ints[10];
     switch (field) {
     case ORC_F_CAND: src = S->cand; sz = slots * 4; break;
@@ -961,6 +976,7 @@ int orc_get(void *h, int32_t field, void *dst, int64_t bytes)
         scal[4] = S->L_nn; scal[5] = S->tau_max64; scal[6] = S->tau_min64;
         scal[7] = (double)S->tau_max; scal[8] = (double)S->tau_min; scal[9] = S->L_gb;
         scal[10] = S->L_ib; scal[11] = (double)S->n_lambda; scal[12] = S->L_rb;
+        scal[13] = (double)S->n_edges / (2.0 * (double)S->n);   /* Edges/n, Sec. VI-A */
         src = scal; sz = sizeof scal; break;
     case ORC_F_INTS:
         ints[0] = S->n; ints[1] = S->k_eff; ints[2] = S->k_pad; ints[3] = S->t;

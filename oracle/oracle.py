@@ -47,7 +47,7 @@ class _Params(C.Structure):
                 ("q_level", C.c_double), ("p_best", C.c_double), ("logw_clip", C.c_double),
                 ("degree_target", C.c_int32), ("local_search", C.c_int32),
                 ("baseline_scope", C.c_int32), ("ls_k", C.c_int32), ("schedule", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("kappa_mode", C.c_int32), ("seed", C.c_uint64)]
 
 
 F = dict(cand=1, cdist=2, conf=3, base=4, evid=5, logev=6, W=7, tau=8, choice=9,
@@ -112,7 +112,7 @@ class _InstHolder:
 def _params(p) -> _Params:
     return _Params(p.m, p.k, p.iterations, p.alpha, p.beta, p.rho, p.theta_h, p.eps, p.c_cap,
                    p.q_level, p.p_best, p.logw_clip, p.degree_target, p.local_search,
-                   p.baseline_scope, p.ls_k, getattr(p, "schedule", 0), p.seed)
+                   p.baseline_scope, p.ls_k, getattr(p, "schedule", 0), getattr(p, "kappa_mode", 0), p.seed)
 
 
 class Oracle:
@@ -169,9 +169,9 @@ class Oracle:
         return self._get_raw(field, dt, int(np.prod(shp))).reshape(shp)
 
     def scalars(self) -> dict:
-        s = self._get_raw("scalars", np.float64, 13)
+        s = self._get_raw("scalars", np.float64, 14)
         keys = ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
-                "tau_min", "L_gb", "L_ib", "n_lambda", "L_rb")
+                "tau_min", "L_gb", "L_ib", "n_lambda", "L_rb", "edges_per_n")
         return dict(zip(keys, s.tolist()))
 
     def ints(self) -> dict:

@@ -73,6 +73,7 @@ class Params:
     ls_k: int = 20
     seed: int = 0
     schedule: int = 0                 # 1: MMAS u_gb schedule and restarts (Sec. III-B)
+    kappa_mode: int = 0               # 0: eq. kappa; 1: fixed kappa = 1; 2: no cap factor (Sec. V-D)
 
 
 # ----------------------------------------------------------------------------- points

@@ -356,3 +356,67 @@ def test_choice_alpha_power(orc):
                 continue
             assert ch[i, c] == ref, (i, c)
     assert skipped <= 2
+
+
+# ---------------------------------------------------------------------------
+# The ablation variants of Sec. V-D (kappa_mode) and the candidate density
+# Edges/n of Sec. VI-A.
+
+def test_fixed_kappa_one_weights(orc):
+    """kappa_mode 1 ("fixed kappa = 1"): W = fl32(eta^2 * e) wherever ln e is
+    below the clip; on the hand-worked row 0, eta = 8/c and e = 5, 3, 1, 1, 1."""
+    mpmath = pytest.importorskip("mpmath")
+    pts, H = _hand_instance()
+    p = params(m=2, k=8, iterations=0, rho=0.2, kappa_mode=1)
+    o = orc.Oracle(euclid(pts, H, symmetrize=0), p)
+    assert o.scalars()["kappa"] == 1.0
+    assert list(o.get("W")[0][:5]) == [np.float32(320.0), np.float32(48.0), np.float32(64.0 / 9.0),
+                                       np.float32(4.0), np.float32(64.0 / 25.0)]
+    inst, ps = synth.workload("tsp500")
+    q = ps[0]
+    q.iterations, q.kappa_mode = 0, 1
+    o = orc.Oracle(inst[0], q)
+    assert o.scalars()["kappa"] == 1.0
+    _check_weights(o, q, mpmath, kappa=1.0)
+
+
+def test_no_cap_kappa(orc):
+    """kappa_mode 2 ("no cap"): the cap factor c_cap leaves eq. (kappa), so
+    kappa * q90 = alpha * ln R and kappa is 1/c_cap times the default one."""
+    mpmath = pytest.importorskip("mpmath")
+    inst, ps = synth.workload("tsp500")
+    p = ps[0]
+    p.iterations = 0
+    base = orc.Oracle(inst[0], p).scalars()
+    for alpha in (1.0, 1.5):
+        p.alpha, p.kappa_mode = alpha, 2
+        o = orc.Oracle(inst[0], p)
+        s = o.scalars()
+        assert s["q90"] == base["q90"] and s["Rhat"] == base["Rhat"]
+        assert s["kappa"] * s["q90"] == pytest.approx(alpha * math.log(s["Rhat"]), rel=1e-13)
+        if alpha == 1.0:
+            assert s["kappa"] == pytest.approx(2.0 * base["kappa"], rel=1e-14)
+            _check_weights(o, p, mpmath)
+    p.kappa_mode = 3
+    with pytest.raises(ValueError):
+        orc.Oracle(inst[0], p)
+
+
+def test_edges_per_node(orc):
+    """Edges/n = |{(i, j): h_ij > theta_h}| / (2n) over the heatmap as the decoder
+    reads it (Sec. VI-A), counted here from the dense matrix."""
+    pts, H = _hand_instance()
+    o = orc.Oracle(euclid(pts, H, symmetrize=0), params(m=2, k=8, iterations=0, rho=0.2))
+    assert o.scalars()["edges_per_n"] == 6 / 12
+    o = orc.Oracle(euclid(pts, H, symmetrize=1), params(m=2, k=8, iterations=0, rho=0.2))
+    Hs = (H + H.T) / 2
+    assert o.scalars()["edges_per_n"] == np.count_nonzero(Hs > 1e-4) / 12
+    inst = synth.euclid_instance(5, 300, K=12)
+    Hd = np.zeros((300, 300))
+    for i in range(300):
+        Hd[i, inst.col[inst.rowptr[i]:inst.rowptr[i + 1]]] = inst.val[inst.rowptr[i]:inst.rowptr[i + 1]]
+    Hs = (Hd + Hd.T) * 0.5
+    o = orc.Oracle(inst, params(m=2, k=8, iterations=0, rho=0.2))
+    assert o.scalars()["edges_per_n"] == np.count_nonzero(Hs > 1e-4) / 600
+    o = orc.Oracle(euclid(pts), params(m=2, k=4, iterations=0, rho=0.2))
+    assert o.scalars()["edges_per_n"] == 0.0
