@@ -436,7 +436,7 @@ def run_ours(args):
         def e2e_step():
             heataco._check(L.hac_solve_batch(mh.ins, mh.ps, count, 0, C.c_void_p(ws.data_ptr()),
                                              C.c_size_t(ws.numel()), C.byref(ex2), tptr,
-                                             C.c_void_p(lens.data_ptr()), stat,
+                                             C.c_void_p(lens.data_ptr()), stat, None,
                                              C.c_void_p(stream.cuda_stream)), "solve_batch")
 
         for _ in range(max(1, args.warmup)):

@@ -11,12 +11,15 @@
  * Conventions used by every entry point:
  *   - All functions return an int status: HAC_OK (0) or a negative HAC_E* code.
  *     No function aborts, throws or exits; hac_strerror() names a code.
- *   - The library never allocates device memory.  The caller passes a device
- *     workspace of at least the size reported by the matching *_workspace_size
- *     call (any allocator: cudaMalloc, a PyTorch tensor, a pool).  The
- *     workspace must stay valid, and must not be used by anyone else, until
- *     the handle that was created on it is destroyed.  The library keeps host
- *     memory for its handles only.
+ *   - The caller passes a device workspace of at least the size reported by
+ *     the matching *_workspace_size call (any allocator: cudaMalloc, a
+ *     PyTorch tensor, a pool).  The workspace must stay valid, and must not be
+ *     used by anyone else, until the handle that was created on it is
+ *     destroyed.  The only device allocation the library ever makes is the
+ *     one-shot calls' (hac_solve, hac_solve_batch) when they are given a NULL
+ *     workspace: then they take one from the stream-ordered pool
+ *     (cudaMallocAsync on `stream`) and return it before they return.  The
+ *     library keeps host memory for its handles only.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
  *     device work of a handle is issued on the stream given at its creation.
  *   - Input pointers are host pointers unless `inputs_on_device` is 1, in which
@@ -103,6 +106,10 @@ typedef struct {
  *                   kept) when T_rb has not improved for more than 250
  *                   iterations and the branching factor (band 0.05, per node,
  *                   divided by d*) is below 1 + 1e-5.
+ *   kappa_mode      scale of the evidence factor: 0 (default) eq. kappa,
+ *                   kappa = c_cap*alpha*ln(R)/q90; the two ablation variants
+ *                   of Sec. V-D: 1 "fixed kappa = 1"; 2 "no cap", the cap
+ *                   factor c_cap dropped from eq. kappa (alpha*ln(R)/q90).
  *   seed            key of the instance's Philox stream. */
 typedef struct {
     int32_t m, k, iterations;
@@ -113,12 +120,14 @@ typedef struct {
     int32_t baseline_scope;
     int32_t ls_k;
     int32_t schedule;
+    int32_t kappa_mode;
     uint64_t seed;
 } hac_params;
 
 /* Execution options of a batch (none of them changes any result). */
 typedef struct {
-    int32_t ants_per_warp;    /* 1, 2 or 4 ants share one warp (8-lane segments); 0 = auto */
+    int32_t ants_per_warp;    /* 1, 2 or 4 ants share one warp (8-lane segments), 16 (one ant per
+                                 lane pair) or 32 (one ant per lane); 0 = auto */
     int32_t warps_per_block;  /* construction block size in warps; 0 = auto */
     int32_t use_graph;        /* 1: capture the iteration loop (per-step kernels: 10 iterations
                                  per graph; fused: the concurrent group launches) in a CUDA
@@ -186,9 +195,11 @@ int hac_batch_sync(hac_batch *bt);
  *   IB_TOUR int32 n         last iteration-best tour (after local search)
  *   TOURS  int32  m*n       the m tours of the last iteration
  *   LENS   f64    m         their lengths
- *   SCALARS f64   20        q90, Rhat, kappa, p_x, L_nn, tau_max64, tau_min64,
+ *   SCALARS f64   21        q90, Rhat, kappa, p_x, L_nn, tau_max64, tau_min64,
  *                           tau_max, tau_min, L_gb, L_ib, n_lambda, t, ib_ant,
- *                           n_fallback, k_pad, L_rb, n_restarts, t_restart, u_gb
+ *                           n_fallback, k_pad, L_rb, n_restarts, t_restart, u_gb,
+ *                           edges_per_n (|{(i,j): h_ij > theta_h}| / (2n), the
+ *                           candidate density diagnostic Edges/n of Sec. VI-A)
  *   NBR    int32  n*ls_k    geometric 2-opt neighbour lists
  *   TRACE  f64    5*I       per iteration: ib ant, L_ib, L_gb, L_rb (+inf when
  *                           cleared), code (1: T_rb deposited, 2: restart)
@@ -222,10 +233,10 @@ int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *lau
  * candidate execution layout and returns in *best the layout whose last
  * trial_iters iterations took the least device time (CUDA events on
  * `stream`), with use_graph = 1, and that time per iteration in *ms_per_iter
- * (may be NULL).  Candidates: the fused cluster kernel with 2, 4 or 32 ants
- * per warp, smallest cluster 1, 2 or 4 CTAs, with and without the 32-entry
- * nearest-unvisited lookup list; the per-step kernels with 1, 2 or 4 ants per
- * warp and 4 or 8 warps per block.  No layout changes a result, so the choice
+ * (may be NULL).  Candidates: the fused cluster kernel with 2, 4, 16 or 32
+ * ants per warp, smallest cluster 1, 2 or 4 CTAs, with and without the
+ * 32-entry nearest-unvisited lookup list; the per-step kernels with 1, 2, 4
+ * or 16 ants per warp and 4 or 8 warps per block.  No layout changes a result, so the choice
  * is a matter of speed only; the method's parameters (m, k, ...) are never
  * changed.  Uses `workspace` (hac_batch_workspace_size bytes) for each trial
  * in turn; synchronises `stream`.  Candidates an instance does not support
@@ -240,16 +251,44 @@ int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t co
 int hac_batch_destroy(hac_batch *bt);
 
 /* ------------------------------------------------------------------ one-shot
- * Decode one instance / a batch end to end (create, run, results, destroy) and
- * synchronise.  statuses (count entries, may be NULL) receives per-instance
- * status. */
+ * Decode one instance / a batch end to end: the decoding problem g(H, D) ->
+ * tour of Sec. II-B, by Algorithm 1 (REQUIRE: the distances D, the heatmap H
+ * and the parameters m, I, k, alpha, beta, rho, c_cap of hac_params; ENSURE:
+ * the global-best tour T_gb), each instance run for its own p.iterations.
+ * Create, run, results and destroy in one call; synchronises `stream`.
+ *
+ *   workspace, ws_bytes  device memory of at least hac_batch_workspace_size
+ *                   bytes, or NULL: the call then allocates that much from the
+ *                   stream-ordered pool (cudaMallocAsync on `stream`) and
+ *                   frees it before it returns (HAC_ENOMEM if the pool cannot
+ *                   supply it).  With a NULL workspace nothing is required of
+ *                   the caller but host buffers, so a plain C program can
+ *                   decode host inputs (inputs_on_device = 0) in one call.
+ *   best_tour(s)    caller-owned host buffers of n (n_b) int32: T_gb
+ *   best_len(s)     L_gb (eq. tour_length), FP64
+ *   statuses        count entries, may be NULL: the call's status per instance
+ *   stats           1 (count) entries, may be NULL: per-instance counters
+ *                   (hac_stats), filled on success
+ *   exec            execution layout (hac_solve_batch; NULL = defaults)
+ */
+typedef struct {
+    int32_t iterations;      /* MMAS iterations run (the instance's p.iterations) */
+    int32_t restarts;        /* pheromone restarts (schedule = 1) */
+    int64_t ant_steps;       /* sum over the iterations of m * n construction steps */
+    int64_t fallback_steps;  /* steps that took the nearest-unvisited rule (Alg. 2) */
+    double kappa;            /* the evidence scale used (eq. kappa or its kappa_mode variant) */
+    double edges_per_n;      /* candidate density |{h_ij > theta_h}| / (2n) (Sec. VI-A) */
+    double L_nn;             /* length of the initial tour T_NN (Alg. 1) */
+    double seconds;          /* wall time of the whole call (the same for every instance) */
+} hac_stats;
+
 int hac_solve(const hac_instance *in, const hac_params *p, int32_t inputs_on_device,
               void *workspace, size_t ws_bytes, int32_t *best_tour, double *best_len,
-              void *stream);
+              hac_stats *stats, void *stream);
 int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count,
                     int32_t inputs_on_device, void *workspace, size_t ws_bytes,
                     const hac_exec *exec, int32_t *const *best_tours, double *best_lens,
-                    int32_t *statuses, void *stream);
+                    int32_t *statuses, hac_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ serving
  * Continuous batching of decode requests (the paper has no serving layer;
@@ -281,8 +320,8 @@ int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count
  *                   SM for large n); those requests all run the smallest
  *                   budget among them each tick
  *   step_ants_per_warp, step_warps_per_block
- *                   layout of that route (0 -> 1 and 8; 1, 2 or 4 and 1..8)
- *   exec            ants_per_warp (0 -> 4; 2, 4 or 32), cluster_log2 (the
+ *                   layout of that route (0 -> 1 and 8; 1, 2, 4 or 16 and 1..8)
+ *   exec            ants_per_warp (0 -> 4; 2, 4, 16 or 32), cluster_log2 (the
  *                   smallest cluster size, log2), fallback_list (0 or 32);
  *                   fused is implied, the other fields are ignored */
 typedef struct {

@@ -1,8 +1,10 @@
 // Host orchestration behind the C ABI of heataco.h: workspace layout, input
 // upload and validation, work tables, the iteration loop (optionally captured
-// in a CUDA graph) and read-back.  No device memory is allocated here: every
-// device array is a slice of the caller's workspace.
+// in a CUDA graph) and read-back.  Every device array is a slice of the
+// caller's workspace; only a one-shot call given no workspace takes one from
+// the stream-ordered pool for its own duration.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -92,99 +94,20 @@ int fold_events(hac_batch *bt)
 
 static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
 {
-    const int apw = bt->ex.ants_per_warp == 2 ? 2 : bt->ex.ants_per_warp == 32 ? 32 : 4;
+    const int q = bt->ex.ants_per_warp;
+    const int apw = (q == 2 || q == 16 || q == 32) ? q : 4;
     if (apw != bt->ex.ants_per_warp) return HAC_EUNSUPPORTED;   // the fused kernel has no 1-ant-per-warp form
     std::vector<int> members(bt->count);
     for (int b = 0; b < bt->count; ++b) members[b] = b;
     return plan_groups(bt->zs, members, apw, bt->ex.cluster_log2, bt->ex.fallback_list, bt->groups, order);
 }
 
-extern "C" {
-
-int hac_version(void) { return 1; }
-
-int hac_last_cuda_error(void) { return g_last_cuda; }
-
-const char *hac_strerror(int status)
+// Everything hac_batch_create does after allocating the handle; on failure
+// the caller releases the handle (and the streams and events made so far).
+static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params *ps, int32_t count,
+                       int32_t inputs_on_device, void *workspace, const hac_exec &ex, void *stream,
+                       const Plan &P)
 {
-    switch (status) {
-    case HAC_OK: return "ok";
-    case HAC_EINVAL: return "invalid argument or malformed instance";
-    case HAC_ENOMEM: return "workspace too small or host allocation failed";
-    case HAC_ECUDA: return "CUDA runtime error";
-    case HAC_ETIMEOUT: return "device-side wait timed out";
-    case HAC_EUNSUPPORTED: return "unsupported combination";
-    case HAC_EBUSY: return "busy";
-    default: return "unknown status";
-    }
-}
-
-int hac_params_default(hac_params *p, int32_t kind)
-{
-    if (!p || (kind != 0 && kind != 1)) return HAC_EINVAL;
-    std::memset(p, 0, sizeof *p);
-    p->m = 32; p->k = 20; p->iterations = 5000;
-    p->alpha = 1.0; p->beta = 2.0; p->rho = kind == 1 ? 0.2 : 0.8;
-    p->theta_h = 1e-4; p->eps = 1e-9; p->c_cap = 0.5; p->q_level = 0.90;
-    p->p_best = 0.05; p->logw_clip = 30.0;
-    p->degree_target = kind == 1 ? 1 : 2;
-    p->local_search = 0; p->baseline_scope = 0; p->ls_k = 20; p->seed = 0;
-    return HAC_OK;
-}
-
-int hac_exec_default(hac_exec *e)
-{
-    if (!e) return HAC_EINVAL;
-    e->ants_per_warp = 0;
-    e->warps_per_block = 0;
-    e->use_graph = 1;
-    e->fused = 0;
-    e->fallback_list = 0;
-    e->profile = 0;
-    e->cluster_log2 = 0;
-    return HAC_OK;
-}
-
-int hac_batch_workspace_size(const hac_instance *ins, const hac_params *ps, int32_t count,
-                             int32_t inputs_on_device, size_t *bytes)
-{
-    if (!bytes) return HAC_EINVAL;
-    Plan P;
-    int st = plan_batch(ins, ps, count, inputs_on_device, P);
-    if (st) return st;
-    *bytes = P.total;
-    return HAC_OK;
-}
-
-int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t count,
-                     int32_t inputs_on_device, void *workspace, size_t ws_bytes,
-                     const hac_exec *exec, void *stream, hac_batch **out)
-{
-    if (!out) return HAC_EINVAL;
-    *out = nullptr;
-    Plan P;
-    int st = plan_batch(ins, ps, count, inputs_on_device, P);
-    if (st) return st;
-    if (!workspace || ws_bytes < P.total) return HAC_ENOMEM;
-    if (!inputs_on_device)
-        for (int b = 0; b < count; ++b)
-            if ((st = check_host_data(ins[b]))) return st;
-    hac_exec ex;
-    hac_exec_default(&ex);
-    if (exec) ex = *exec;
-    if (ex.ants_per_warp == 0) ex.ants_per_warp = 4;
-    if (ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 32)
-        return HAC_EINVAL;
-    if (ex.warps_per_block == 0) ex.warps_per_block = 4;
-    if (ex.warps_per_block < 1 || ex.warps_per_block > 8) return HAC_EINVAL;
-    if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
-    if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
-    if (ex.ants_per_warp == 32)   // step-major tours: 2-opt on every ant needs them ant by ant
-        for (int b = 0; b < count; ++b)
-            if (ps[b].local_search == 2) return HAC_EUNSUPPORTED;
-
-    hac_batch *bt = new (std::nothrow) hac_batch;
-    if (!bt) return HAC_ENOMEM;
     bt->count = count;
     bt->stream = (cudaStream_t)stream;
     bt->ex = ex;
@@ -268,11 +191,101 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
         return launch_prep(bt->d_inst, bt->hi.data(), count, bt->d_rowmap, bt->rowmap_len,
                            bt->d_slotmap, bt->slotmap_len, bt->d_err, s);
     });
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        g_last_cuda = (int)e;
-        delete bt;
-        return HAC_ECUDA;
+    CK(cudaGetLastError());
+    return HAC_OK;
+}
+
+extern "C" {
+
+int hac_version(void) { return 1; }
+
+int hac_last_cuda_error(void) { return g_last_cuda; }
+
+const char *hac_strerror(int status)
+{
+    switch (status) {
+    case HAC_OK: return "ok";
+    case HAC_EINVAL: return "invalid argument or malformed instance";
+    case HAC_ENOMEM: return "workspace too small or host allocation failed";
+    case HAC_ECUDA: return "CUDA runtime error";
+    case HAC_ETIMEOUT: return "device-side wait timed out";
+    case HAC_EUNSUPPORTED: return "unsupported combination";
+    case HAC_EBUSY: return "busy";
+    default: return "unknown status";
+    }
+}
+
+int hac_params_default(hac_params *p, int32_t kind)
+{
+    if (!p || (kind != 0 && kind != 1)) return HAC_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->m = 32; p->k = 20; p->iterations = 5000;
+    p->alpha = 1.0; p->beta = 2.0; p->rho = kind == 1 ? 0.2 : 0.8;
+    p->theta_h = 1e-4; p->eps = 1e-9; p->c_cap = 0.5; p->q_level = 0.90;
+    p->p_best = 0.05; p->logw_clip = 30.0;
+    p->degree_target = kind == 1 ? 1 : 2;
+    p->local_search = 0; p->baseline_scope = 0; p->ls_k = 20; p->seed = 0;
+    return HAC_OK;
+}
+
+int hac_exec_default(hac_exec *e)
+{
+    if (!e) return HAC_EINVAL;
+    e->ants_per_warp = 0;
+    e->warps_per_block = 0;
+    e->use_graph = 1;
+    e->fused = 0;
+    e->fallback_list = 0;
+    e->profile = 0;
+    e->cluster_log2 = 0;
+    return HAC_OK;
+}
+
+int hac_batch_workspace_size(const hac_instance *ins, const hac_params *ps, int32_t count,
+                             int32_t inputs_on_device, size_t *bytes)
+{
+    if (!bytes) return HAC_EINVAL;
+    Plan P;
+    int st = plan_batch(ins, ps, count, inputs_on_device, P);
+    if (st) return st;
+    *bytes = P.total;
+    return HAC_OK;
+}
+
+int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t count,
+                     int32_t inputs_on_device, void *workspace, size_t ws_bytes,
+                     const hac_exec *exec, void *stream, hac_batch **out)
+{
+    if (!out) return HAC_EINVAL;
+    *out = nullptr;
+    Plan P;
+    int st = plan_batch(ins, ps, count, inputs_on_device, P);
+    if (st) return st;
+    if (!workspace || ws_bytes < P.total) return HAC_ENOMEM;
+    if (!inputs_on_device)
+        for (int b = 0; b < count; ++b)
+            if ((st = check_host_data(ins[b], ps[b]))) return st;
+    hac_exec ex;
+    hac_exec_default(&ex);
+    if (exec) ex = *exec;
+    if (ex.ants_per_warp == 0) ex.ants_per_warp = 4;
+    if (ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 16 &&
+        ex.ants_per_warp != 32)
+        return HAC_EINVAL;
+    if (ex.warps_per_block == 0) ex.warps_per_block = 4;
+    if (ex.warps_per_block < 1 || ex.warps_per_block > 8) return HAC_EINVAL;
+    if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
+    if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
+    if (ex.ants_per_warp == 32)   // step-major tours: 2-opt on every ant needs them ant by ant
+        for (int b = 0; b < count; ++b)
+            if (ps[b].local_search == 2) return HAC_EUNSUPPORTED;
+
+    hac_batch *bt = new (std::nothrow) hac_batch;
+    if (!bt) return HAC_ENOMEM;
+    st = batch_setup(bt, ins, ps, count, inputs_on_device, workspace, ex, stream, P);
+    if (st) {
+        hac_batch_destroy(bt);
+        return st;
     }
     *out = bt;
     return HAC_OK;
@@ -425,7 +438,7 @@ int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size
         src = D.nbr; sz = n * D.ls_k * 4; break;
     case HAC_F_TRACE: src = D.trace; sz = (size_t)TRACE_W * std::max(D.iters, 1) * 8; break;
     case HAC_F_SCALARS: {
-        if (bytes < 20 * sizeof(double)) return HAC_EINVAL;
+        if (bytes < 21 * sizeof(double)) return HAC_EINVAL;
         InstState S0;
         CK(cudaMemcpy(&S0, D.st, sizeof S0, cudaMemcpyDeviceToHost));
         double *o = (double *)host_dst;
@@ -434,6 +447,7 @@ int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size
         o[9] = S0.L_gb; o[10] = S0.L_ib; o[11] = S0.n_lambda; o[12] = S0.t; o[13] = S0.ib;
         o[14] = (double)S0.n_fallback; o[15] = D.k_pad;
         o[16] = S0.L_rb; o[17] = S0.n_restarts; o[18] = S0.t_restart; o[19] = S0.u_gb;
+        o[20] = (double)S0.n_edges / (2.0 * (double)D.n);
         return HAC_OK;
     }
     default: return HAC_EINVAL;
@@ -519,13 +533,55 @@ int hac_batch_destroy(hac_batch *bt)
 int hac_solve_batch(const hac_instance *ins, const hac_params *ps, int32_t count,
                     int32_t inputs_on_device, void *workspace, size_t ws_bytes,
                     const hac_exec *exec, int32_t *const *best_tours, double *best_lens,
-                    int32_t *statuses, void *stream)
+                    int32_t *statuses, hac_stats *stats, void *stream)
 {
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    void *own = nullptr;   // stream-ordered workspace of a call given none
+    int st = HAC_OK;
+    if (!workspace) {
+        st = hac_batch_workspace_size(ins, ps, count, inputs_on_device, &ws_bytes);
+        if (!st) {
+            cudaError_t e = cudaMallocAsync(&own, ws_bytes, s);
+            if (e != cudaSuccess) {
+                g_last_cuda = (int)e;
+                cudaGetLastError();
+                st = HAC_ENOMEM;
+                own = nullptr;
+            }
+            workspace = own;
+        }
+    }
     hac_batch *bt = nullptr;
-    int st = hac_batch_create(ins, ps, count, inputs_on_device, workspace, ws_bytes, exec, stream, &bt);
+    if (!st) st = hac_batch_create(ins, ps, count, inputs_on_device, workspace, ws_bytes, exec, stream, &bt);
     if (!st) st = hac_batch_run(bt);
     if (!st) st = hac_batch_results(bt, best_tours, best_lens);
+    if (!st && stats) {
+        for (int b = 0; b < count; ++b) {
+            InstState S0;
+            cudaError_t e = cudaMemcpy(&S0, bt->hi[b].st, sizeof S0, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { g_last_cuda = (int)e; st = HAC_ECUDA; break; }
+            const Sizes &z = bt->zs[b];
+            hac_stats &o = stats[b];
+            o.iterations = S0.t;
+            o.restarts = S0.n_restarts;
+            o.ant_steps = (int64_t)z.m * z.n * S0.t;
+            o.fallback_steps = (int64_t)S0.n_fallback;
+            o.kappa = S0.kappa;
+            o.edges_per_n = (double)S0.n_edges / (2.0 * (double)z.n);
+            o.L_nn = S0.L_nn;
+        }
+    }
     if (bt) hac_batch_destroy(bt);
+    if (own) {
+        cudaError_t e = cudaFreeAsync(own, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess && !st) { g_last_cuda = (int)e; st = HAC_ECUDA; }
+    }
+    if (!st && stats) {
+        const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int b = 0; b < count; ++b) stats[b].seconds = sec;
+    }
     if (statuses)
         for (int b = 0; b < count; ++b) statuses[b] = st;
     return st;
@@ -542,7 +598,7 @@ int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t co
     if (!workspace || ws_bytes < P.total) return HAC_ENOMEM;
     // candidates: every execution layout (none changes a result)
     std::vector<hac_exec> cands;
-    for (int apw : {4, 2, 32})
+    for (int apw : {16, 4, 2, 32})
         for (int clog = 0; clog <= 2; ++clog)
             for (int fbl : {FBL_LEN, 0}) {
                 hac_exec e;
@@ -550,7 +606,7 @@ int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t co
                 e.fused = 1; e.ants_per_warp = apw; e.cluster_log2 = clog; e.fallback_list = fbl;
                 cands.push_back(e);
             }
-    for (int apw : {4, 2, 1})
+    for (int apw : {16, 4, 2, 1})
         for (int wpb : {4, 8}) {
             hac_exec e;
             hac_exec_default(&e);
@@ -598,11 +654,12 @@ int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t co
 }
 
 int hac_solve(const hac_instance *in, const hac_params *p, int32_t inputs_on_device,
-              void *workspace, size_t ws_bytes, int32_t *best_tour, double *best_len, void *stream)
+              void *workspace, size_t ws_bytes, int32_t *best_tour, double *best_len,
+              hac_stats *stats, void *stream)
 {
     int32_t *tours[1] = {best_tour};
     return hac_solve_batch(in, p, 1, inputs_on_device, workspace, ws_bytes, nullptr, tours,
-                           best_len, nullptr, stream);
+                           best_len, nullptr, stats, stream);
 }
 
 }  // extern "C"

@@ -3,6 +3,7 @@
 // (128-bit loads of ids and choice values).  The per-ant work is build_tours
 // in ant.cuh; this file maps warps to (instance, ants) through the warp table.
 #include "ant_lane.cuh"
+#include "ant_pair.cuh"
 
 namespace hac {
 
@@ -45,6 +46,26 @@ __global__ void __launch_bounds__(256, 1) k_construct_lane(const DevInst *__rest
                          reinterpret_cast<const float2 *>(I.xy));
 }
 
+// one ant per lane pair: warp w of the table builds ants a0..a0+15 of its instance
+template <int NGL>
+__global__ void __launch_bounds__(256, 1) k_construct_pair(const DevInst *__restrict__ insts,
+                                                        const int4 *__restrict__ warpmap, int nwarps,
+                                                        int nwords_max)
+{
+    extern __shared__ unsigned int smem_vis[];
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (gw >= nwarps) return;
+    const int4 wm = warpmap[gw];
+    const DevInst &I = insts[wm.x];
+    const int t = I.st->t;
+    if (t >= I.iters) return;
+    GlobalRows rows{reinterpret_cast<const int4 *>(I.cand), reinterpret_cast<const float4 *>(I.choice),
+                    I.k_pad >> 2, I.n};
+    build_tours_pair<NGL>(I, rows, GlobalList{I.fbl}, t, wm.y, I.m, smem_vis + (size_t)wib * 16 * nwords_max,
+                          nwords_max, reinterpret_cast<const float2 *>(I.xy));
+}
+
 // fallback distances, then every ant's length (one block per instance)
 __global__ void k_lengths(const DevInst *insts)
 {
@@ -84,6 +105,22 @@ int launch_construct(const DevInst *d_inst, const int4 *d_warpmap, int warpmap_l
         if (G <= 3) go(k_construct_lane<3>);
         else if (G <= 5) go(k_construct_lane<5>);
         else go(k_construct_lane<8>);
+        k_lengths<<<count, 256, 0, s>>>(d_inst);
+        return 2;
+    }
+    if (apw == 16) {
+        const int nwords = (max_n + 32) / 32;
+        const size_t smem = (size_t)warps_per_block * 16 * nwords * sizeof(unsigned);
+        const int blocks = (warpmap_len + warps_per_block - 1) / warps_per_block;
+        const int G = max_kp / 4;
+        auto go = [&](auto kern) {
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kern<<<blocks, warps_per_block * 32, smem, s>>>(d_inst, d_warpmap, warpmap_len, nwords);
+        };
+        if (G <= 4) go(k_construct_pair<2>);
+        else if (G <= 6) go(k_construct_pair<3>);
+        else go(k_construct_pair<4>);
         k_lengths<<<count, 256, 0, s>>>(d_inst);
         return 2;
     }

@@ -19,6 +19,7 @@
 #include <cooperative_groups.h>
 
 #include "ant_lane.cuh"
+#include "ant_pair.cuh"
 #include "iter.cuh"
 #include "twoopt.cuh"
 
@@ -47,7 +48,8 @@ __host__ __device__ inline size_t fused_table_bytes(int rows_cap, int kp_cap)
     return ch + ix;
 }
 
-// APW ants per warp: 2 or 4 (warp segments, ant.cuh) or 32 (one ant per lane,
+// APW ants per warp: 2 or 4 (warp segments, ant.cuh), 16 (one ant per lane
+// pair, ant_pair.cuh, NG slot groups per lane) or 32 (one ant per lane,
 // ant_lane.cuh, NG candidate groups).  Shared memory per CTA:
 //   choice rows (FP32) | candidate ids (uint16) | visited masks |
 //   coordinates (optional) | lookup lists (uint16, optional)
@@ -117,6 +119,9 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
             if constexpr (APW == 32) {
                 if (list_shared) build_tours_lane<NG>(I, rows, clist, t, a_first, a_hi, vis_w, xy_scan);
                 else build_tours_lane<NG>(I, rows, glist, t, a_first, a_hi, vis_w, xy_scan);
+            } else if constexpr (APW == 16) {
+                if (list_shared) build_tours_pair<NG>(I, rows, clist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
+                else build_tours_pair<NG>(I, rows, glist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
             } else {
                 if (list_shared) build_tours<APW>(I, rows, clist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
                 else build_tours<APW>(I, rows, glist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
@@ -246,6 +251,12 @@ cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, const in
         if (G <= 3) { CLUSTER_SWITCH(32, 3) }
         if (G <= 5) { CLUSTER_SWITCH(32, 5) }
         CLUSTER_SWITCH(32, 8)
+    }
+    if (apw == 16) {
+        const int G = kp_cap / 4;   // slot groups; lane h of a pair holds groups 2j + h
+        if (G <= 4) { CLUSTER_SWITCH(16, 2) }
+        if (G <= 6) { CLUSTER_SWITCH(16, 3) }
+        CLUSTER_SWITCH(16, 4)
     }
     if (apw == 2) { CLUSTER_SWITCH(2, 0) }
     CLUSTER_SWITCH(4, 0)

@@ -37,12 +37,13 @@ struct InstState {
     int32_t u_gb;       // T_rb deposits when the iteration is a multiple of this
     int32_t n_restarts;
     unsigned long long bf_count;   // branching-factor count of the current check
+    unsigned long long n_edges;    // sum of |P_i|: heatmap entries above theta_h (Edges/n diagnostic)
 };
 
 // Device view of one instance: sizes, parameters and pointers into the workspace.
 struct DevInst {
     int32_t n, kind, k, k_eff, k_pad, m, iters, ls_k;
-    int32_t degree_target, local_search, baseline_scope, symmetrize, h_half, schedule;
+    int32_t degree_target, local_search, baseline_scope, symmetrize, h_half, schedule, kappa_mode;
     uint64_t seed;
     double alpha, beta, rho, theta_h, eps, c_cap, q_level, p_best, logw_clip;
     // inputs

@@ -61,6 +61,7 @@ inline int check_params(const hac_instance &in, const hac_params &p)
     if (!(p.c_cap >= 0.0) || !(p.logw_clip > 0.0)) return HAC_EINVAL;
     if (p.baseline_scope != 0 && p.baseline_scope != 1) return HAC_EINVAL;
     if (p.schedule != 0 && p.schedule != 1) return HAC_EINVAL;
+    if (p.kappa_mode < 0 || p.kappa_mode > 2) return HAC_EINVAL;
     if (p.local_search < 0 || p.local_search > 2) return HAC_EINVAL;
     if (p.local_search) {
         if (in.kind != 0) return HAC_EUNSUPPORTED;
@@ -70,8 +71,12 @@ inline int check_params(const hac_instance &in, const hac_params &p)
     return HAC_OK;
 }
 
+// |x|, |y| bound with local search: the 2-opt pre-test's FP32 squared
+// differences stay finite (2e18^2 * 2 < FLT_MAX)
+constexpr double LS_COORD_MAX = 1e18;
+
 // full check of host-resident inputs (device inputs are checked by a kernel)
-inline int check_host_data(const hac_instance &in)
+inline int check_host_data(const hac_instance &in, const hac_params &p)
 {
     const int n = in.n;
     if (in.h_rowptr[0] != 0) return HAC_EINVAL;
@@ -97,6 +102,9 @@ inline int check_host_data(const hac_instance &in)
     }
     if (in.kind == 0) {
         for (long long q = 0; q < 2LL * n; ++q) if (!finite_f(in.coords[q])) return HAC_EINVAL;
+        if (p.local_search)
+            for (long long q = 0; q < 2LL * n; ++q)
+                if (!(std::fabs((double)in.coords[q]) <= LS_COORD_MAX)) return HAC_EINVAL;
     } else {
         for (long long q = 0; q < (long long)n * n; ++q) if (!finite_f(in.cost[q])) return HAC_EINVAL;
     }
@@ -261,6 +269,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
     D.degree_target = p.degree_target; D.local_search = p.local_search;
     D.baseline_scope = p.baseline_scope; D.symmetrize = in.symmetrize; D.h_half = in.h_dtype;
     D.schedule = p.schedule;
+    D.kappa_mode = p.kappa_mode;
     D.seed = p.seed;
     D.nnz = (int32_t)z.nnz;
     D.alpha = p.alpha; D.beta = p.beta; D.rho = p.rho; D.theta_h = p.theta_h; D.eps = p.eps;

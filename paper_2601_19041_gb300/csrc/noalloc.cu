@@ -63,5 +63,5 @@ extern "C" int hac_solve_noalloc(const hac_instance *in, const hac_params *p,
     ex.profile = 0;
     int32_t *tours[1] = {best_tour};
     return hac_solve_batch(in, p, 1, inputs_on_device, scratch, NOALLOC_BYTES, &ex, tours,
-                           best_len, nullptr, stream);
+                           best_len, nullptr, nullptr, stream);
 }

@@ -50,6 +50,8 @@ __global__ void k_validate(const DevInst *insts, const int2 *rowmap, int *err)
     if (I.kind == 0 && lane == 0) {
         float2 a = reinterpret_cast<const float2 *>(I.xy)[i];
         if (!isfinite(a.x) || !isfinite(a.y)) set_err(err, HAC_EINVAL);
+        // with local search the 2-opt pre-test needs finite FP32 squared differences
+        if (I.local_search && !(fabsf(a.x) <= 1e18f && fabsf(a.y) <= 1e18f)) set_err(err, HAC_EINVAL);
     }
     if (I.kind == 1)
         for (int j = lane; j < I.n; j += 32)
@@ -581,6 +583,16 @@ __global__ void k_kappa(const DevInst *insts)
     __syncthreads();
     long long N = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) N += wcount[w];
+    __syncthreads();
+    // Edges/n diagnostic (Sec. VI-A): sum of the support-set sizes |P_i|
+    long long ne = 0;
+    for (int i = threadIdx.x; i < I.n; i += blockDim.x) ne += I.mem_cnt[i];
+    for (int o = 16; o; o >>= 1) ne += __shfl_xor_sync(FULL, ne, o);
+    __shared__ long long wne[32];
+    if ((threadIdx.x & 31) == 0) wne[threadIdx.x >> 5] = ne;
+    __syncthreads();
+    long long NE = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) NE += wne[w];
     double q = 0.0;
     if (N > 0) {
         double h = __dmul_rn((double)(N - 1), I.q_level);
@@ -600,10 +612,15 @@ __global__ void k_kappa(const DevInst *insts)
         double R;
         if (I.local_search) R = __dmul_rn(2.0, (double)I.n);
         else R = __ddiv_rn(__dmul_rn(__ddiv_rn((double)(I.k_eff - 1), 2.0), px), __dsub_rn(1.0, px));
+        // eq. kappa; kappa_mode 1 and 2 are the ablation variants of Sec. V-D
+        // (fixed kappa = 1; the cap factor c_cap dropped)
         double kap = 0.0;
-        if (q > 0.0 && R > 1.0) kap = __ddiv_rn(__dmul_rn(__dmul_rn(I.c_cap, I.alpha), det_ln(R)), q);
+        if (I.kappa_mode == 1) kap = 1.0;
+        else if (q > 0.0 && R > 1.0)
+            kap = __ddiv_rn(__dmul_rn(I.kappa_mode == 2 ? I.alpha : __dmul_rn(I.c_cap, I.alpha), det_ln(R)), q);
         st->q90 = q; st->Rhat = R; st->kappa = kap; st->p_x = px;
         st->n_lambda = (int)N;
+        st->n_edges = (unsigned long long)NE;
     }
 }
 

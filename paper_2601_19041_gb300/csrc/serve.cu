@@ -364,10 +364,11 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
         return HAC_EINVAL;
     const int s_apw = c.step_ants_per_warp ? c.step_ants_per_warp : 1;
     const int s_wpb = c.step_warps_per_block ? c.step_warps_per_block : 8;
-    if ((s_apw != 1 && s_apw != 2 && s_apw != 4) || s_wpb < 1 || s_wpb > 8) return HAC_EINVAL;
+    if ((s_apw != 1 && s_apw != 2 && s_apw != 4 && s_apw != 16) || s_wpb < 1 || s_wpb > 8) return HAC_EINVAL;
     hac_exec ex = c.exec;
     if (ex.ants_per_warp == 0) ex.ants_per_warp = 4;
-    if (ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 32) return HAC_EINVAL;
+    if (ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 16 && ex.ants_per_warp != 32)
+        return HAC_EINVAL;
     if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
     if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
     ex.fused = 1;
@@ -465,7 +466,7 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     int st = instance_sizes(*in, *p, 0, z);
     if (st) return st;
     if (z.n > sv->cfg.max_n) return HAC_EINVAL;
-    if ((st = check_host_data(*in))) return st;
+    if ((st = check_host_data(*in, *p))) return st;
     const int route = sv->cfg.step_min_n > 0 && z.n >= sv->cfg.step_min_n ? 1 : 0;
     if (!route && (st = fits_fused(sv, z))) return st;
     if (!route && sv->ex.ants_per_warp == 32 && z.ls == 2) return HAC_EUNSUPPORTED;   // step-major tours

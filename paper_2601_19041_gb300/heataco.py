@@ -21,7 +21,7 @@ FIELDS = dict(CAND=1, CDIST=2, CONF=3, BASE=4, EVID=5, W=6, TAU=7, CHOICE=8, NN_
               GB_TOUR=10, IB_TOUR=11, TOURS=12, LENS=13, SCALARS=14, NBR=15, TRACE=16)
 SCALAR_KEYS = ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
                "tau_min", "L_gb", "L_ib", "n_lambda", "t", "ib", "n_fallback", "k_pad", "L_rb", "n_restarts",
-               "t_restart", "u_gb")
+               "t_restart", "u_gb", "edges_per_n")
 
 
 class HeatACOError(RuntimeError):
@@ -47,13 +47,22 @@ class hac_params(C.Structure):
                 ("q_level", C.c_double), ("p_best", C.c_double), ("logw_clip", C.c_double),
                 ("degree_target", C.c_int32), ("local_search", C.c_int32),
                 ("baseline_scope", C.c_int32), ("ls_k", C.c_int32), ("schedule", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("kappa_mode", C.c_int32), ("seed", C.c_uint64)]
 
 
 class hac_exec(C.Structure):
     _fields_ = [("ants_per_warp", C.c_int32), ("warps_per_block", C.c_int32),
                 ("use_graph", C.c_int32), ("fused", C.c_int32), ("fallback_list", C.c_int32),
                 ("profile", C.c_int32), ("cluster_log2", C.c_int32)]
+
+
+class hac_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("ant_steps", C.c_int64),
+                ("fallback_steps", C.c_int64), ("kappa", C.c_double), ("edges_per_n", C.c_double),
+                ("L_nn", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class hac_server_cfg(C.Structure):
@@ -87,10 +96,10 @@ SIGNATURES = {
     "hac_batch_kernel_time": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double),
                                         C.POINTER(C.c_int64)]),
     "hac_solve": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_void_p,
-                            C.c_size_t, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+                            C.c_size_t, C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
     "hac_solve_batch": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_int32,
                                   C.c_void_p, C.c_size_t, C.POINTER(hac_exec), C.POINTER(C.c_void_p),
-                                  C.c_void_p, C.c_void_p, C.c_void_p]),
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "hac_solve_noalloc": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32,
                                     C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "hac_batch_autotune": (C.c_int, [C.POINTER(hac_instance), C.POINTER(hac_params), C.c_int32, C.c_int32,
@@ -185,7 +194,7 @@ class _Marshal:
 def to_c_params(p) -> hac_params:
     return hac_params(p.m, p.k, p.iterations, p.alpha, p.beta, p.rho, p.theta_h, p.eps, p.c_cap,
                       p.q_level, p.p_best, p.logw_clip, p.degree_target, p.local_search,
-                      p.baseline_scope, p.ls_k, getattr(p, "schedule", 0), p.seed)
+                      p.baseline_scope, p.ls_k, getattr(p, "schedule", 0), getattr(p, "kappa_mode", 0), p.seed)
 
 
 def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0, profile=0,
@@ -282,7 +291,7 @@ class Batch:
             "TAU": (np.float32, (n, kp)), "CHOICE": (np.float32, (n, kp)),
             "NN_TOUR": (np.int32, (n,)), "GB_TOUR": (np.int32, (n,)), "IB_TOUR": (np.int32, (n,)),
             "TOURS": (np.int32, (m, n)), "LENS": (np.float64, (m,)),
-            "SCALARS": (np.float64, (20,)), "NBR": (np.int32, (n, p.ls_k)),
+            "SCALARS": (np.float64, (21,)), "NBR": (np.int32, (n, p.ls_k)),
             "TRACE": (np.float64, (max(p.iterations, 1), 5)),
         }[field]
 
@@ -350,6 +359,18 @@ def solve_batch(instances, params, exec_=None, inputs_on_device=False):
 def solve(instance, params, exec_=None):
     tours, lens = solve_batch([instance], [params], exec_)
     return tours[0], float(lens[0])
+
+
+def hac_solve(instance, params, stream=None):
+    """hac_solve with host inputs and no workspace (the library takes one from
+    the stream-ordered pool for the call): (T_gb, L_gb, stats dict)."""
+    m = _Marshal([instance], [params], False)
+    tour = np.empty(instance.n, np.int32)
+    length = C.c_double(0.0)
+    st = hac_stats()
+    _check(_lib().hac_solve(m.ins, m.ps, 0, None, 0, tour.ctypes.data, C.byref(length), C.byref(st),
+                            None if stream is None else C.c_void_p(stream)), "hac_solve")
+    return tour, length.value, st.as_dict()
 
 
 # ------------------------------------------------------------------ serving

@@ -38,7 +38,7 @@ def prep_equal(bt, b, o):
         assert np.array_equal(g, r), f"{f}: {np.argwhere(g != r)[:5]}"
     gs, os_ = bt.scalars(b), o.scalars()
     for key in ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
-                "tau_min", "n_lambda"):
+                "tau_min", "n_lambda", "edges_per_n"):
         assert gs[key] == os_[key], key
 
 
@@ -108,6 +108,9 @@ CASES = {
     # zero-length edges and the longest neighbour list
     "two_opt_dup": lambda: (euclid(np.repeat(_pts(28, 45), 2, axis=0)),
                             params(m=8, k=8, iterations=5, rho=0.2, local_search=1, ls_k=32, seed=24)),
+    # the ablation variants of Sec. V-D: fixed kappa = 1, and kappa without the cap factor
+    "kappa_fixed_one": lambda: (synth.euclid_instance(29, 240, K=50), params(m=12, k=20, iterations=7, rho=0.2, seed=25, kappa_mode=1)),
+    "kappa_no_cap": lambda: (synth.euclid_instance(30, 260, K=50), params(m=12, k=20, iterations=7, rho=0.2, seed=26, kappa_mode=2)),
     "clustered": lambda: (synth.euclid_instance(25, 300, K=50, family="gmm"), params(m=12, k=20, iterations=6, rho=0.2, seed=19)),
     "grid": lambda: (synth.euclid_instance(26, 289, K=50, family="grid"), params(m=12, k=20, iterations=6, rho=0.2, seed=20)),
 }
@@ -120,7 +123,7 @@ def test_case_parity(hac, orc, name):
 
 
 @pytest.mark.parametrize("apw,wpb,graph,fbl", [(1, 4, 1, 0), (2, 8, 0, 32), (4, 2, 1, 32), (4, 8, 0, 0),
-                                              (32, 4, 1, 32), (32, 2, 0, 0)])
+                                              (16, 4, 1, 32), (16, 8, 0, 0), (32, 4, 1, 32), (32, 2, 0, 0)])
 def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph, fbl):
     inst = synth.euclid_instance(31, 410, K=50)
     p = params(m=21, k=20, iterations=23, rho=0.2, seed=3)
@@ -128,12 +131,14 @@ def test_exec_variants_do_not_change_results(hac, orc, apw, wpb, graph, fbl):
 
 
 FUSED = [dict(apw=2, clog=0, fbl=32), dict(apw=4, clog=1, fbl=0), dict(apw=4, clog=3, fbl=32),
-         dict(apw=2, clog=2, fbl=32), dict(apw=32, clog=0, fbl=32), dict(apw=32, clog=2, fbl=0)]
+         dict(apw=2, clog=2, fbl=32), dict(apw=16, clog=0, fbl=32), dict(apw=16, clog=1, fbl=0),
+         dict(apw=16, clog=3, fbl=32), dict(apw=32, clog=0, fbl=32), dict(apw=32, clog=2, fbl=0)]
 
 
 @pytest.mark.parametrize("cfg", FUSED, ids=lambda c: f"apw{c['apw']}_C{1 << c['clog']}_fbl{c['fbl']}")
 @pytest.mark.parametrize("name", ["sym50nn_k20", "sym10nn_k10_ragged", "k32", "k7_pad", "n3",
-                                  "empty_heatmap", "atsp", "two_opt", "two_opt_grid", "alpha_beta_powers"])
+                                  "empty_heatmap", "atsp", "two_opt", "two_opt_grid", "alpha_beta_powers",
+                                  "kappa_no_cap"])
 def test_fused_kernel_parity(hac, orc, name, cfg):
     inst, p = CASES[name]()
     ex = hac.make_exec(cfg["apw"], 0, 1, fused=1, fallback_list=cfg["fbl"], cluster_log2=cfg["clog"])
@@ -148,7 +153,9 @@ def test_fused_mixed_batch_groups(hac, orc):
         ps.append(params(m=m, k=k, iterations=3 + b, rho=0.2, seed=170 + b))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(4, 0, 1, fused=1, fallback_list=32))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(32, 0, 1, fused=1, fallback_list=32))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(16, 0, 1, fused=1, fallback_list=32))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(32, 4, 1, fused=0, fallback_list=32))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(16, 4, 1, fused=0, fallback_list=32))
 
 
 def test_mixed_batch_parity(hac, orc):
@@ -299,3 +306,21 @@ def test_two_opt_every_ant_rejects_lane_mode(hac):
     with pytest.raises(hac.HeatACOError) as e:
         hac.Batch([inst], [p], hac.make_exec(32, 0, 1, fused=1))
     assert e.value.status == hac.HAC_EUNSUPPORTED
+
+
+def test_hac_solve_host_buffers_without_workspace(hac, orc):
+    """The one-shot call of the decoding problem (Sec. II-B, Algorithm 1) with
+    host inputs and no workspace: the library takes one from the stream-ordered
+    pool; tour, length and the stats equal the oracle's."""
+    for inst, p in (CASES["sym50nn_k20"](), CASES["two_opt"](), CASES["atsp"]()):
+        tour, length, st = hac.hac_solve(inst, p)
+        o = orc.Oracle(inst, p).iterate(p.iterations)
+        assert np.array_equal(tour, o.get("gb_tour"))
+        assert length == o.scalars()["L_gb"]
+        assert st["iterations"] == p.iterations
+        assert st["ant_steps"] == p.m * inst.n * p.iterations
+        assert st["fallback_steps"] == o.ints()["n_fallback"]
+        assert st["kappa"] == o.scalars()["kappa"]
+        assert st["edges_per_n"] == o.scalars()["edges_per_n"]
+        assert st["L_nn"] == o.scalars()["L_nn"]
+        assert st["seconds"] > 0.0

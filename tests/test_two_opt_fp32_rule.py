@@ -55,6 +55,9 @@ def point_sets():
     yield "tiny", (rng.random((3000, 2)) * 1e-5).astype(np.float32)
     yield "tiny_offset", (0.5 + rng.random((3000, 2)) * 2e-4).astype(np.float32)
     yield "large", (rng.random((3000, 2)) * 1e4).astype(np.float32)
+    # the largest coordinates accepted with local search (|x|, |y| <= 1e18):
+    # FP32 squared differences stay finite
+    yield "huge", ((rng.random((3000, 2)) * 2.0 - 1.0) * 1e18).astype(np.float32)
     yield "near_dup", (np.repeat(base, 4, axis=0) + rng.normal(0, 1e-7, (1600, 2))).astype(np.float32)
     yield "dup", np.repeat(base, 3, axis=0).astype(np.float32)
 
@@ -69,6 +72,9 @@ def test_fp32_classes_never_contradict_fp64(name, pts):
     gain = ((Da - Dab) + Dbb) - Dn
 
     # FP32 distances: computed in FP32, or FP64 rounded once (both kinds are stored)
+    with np.errstate(over="raise"):
+        for x in (d32(a, an), d32(an, bn), Dab.astype(np.float32)):
+            assert np.all(np.isfinite(x)), name
     for x32, x64 in ((d32(a, an), Da), (d32(an, bn), Dn), (Dab.astype(np.float32), Dab)):
         ok = x64 > 1e-30
         rel = np.abs(x32[ok].astype(np.float64) - x64[ok]) / x64[ok]
@@ -108,3 +114,18 @@ def test_band_is_narrow():
     a, an, b, bn = (pts[i[keep]] for i in idx)
     c = gain_class(d32(a, an), d64(a, b).astype(np.float32), d32(b, bn), d32(an, bn))
     assert np.mean(c == 1) < 1e-4
+
+
+def test_local_search_rejects_coordinates_beyond_the_fp32_range(orc):
+    """Above |x| = 1e18 the FP32 squared differences of the pre-test could
+    overflow, so the decoder refuses such instances when it runs 2-opt (and
+    accepts them without local search)."""
+    from helpers import euclid, params
+    pts = np.random.default_rng(3).random((12, 2)).astype(np.float32)
+    ok = orc.Oracle(euclid(pts * np.float32(1e18)), params(m=2, k=4, iterations=1, rho=0.2, local_search=1, ls_k=5))
+    assert ok.n == 12
+    big = pts.copy()
+    big[3, 1] = np.float32(3e18)
+    with pytest.raises(ValueError):
+        orc.Oracle(euclid(big), params(m=2, k=4, iterations=1, rho=0.2, local_search=1, ls_k=5))
+    orc.Oracle(euclid(big), params(m=2, k=4, iterations=1, rho=0.2))
