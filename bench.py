@@ -208,27 +208,80 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle
 
+def cpu_model():
+    """The host CPU's name from /proc/cpuinfo (model name on x86, implementer/part on Arm)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return None
+    for key in ("model name", "Model name"):
+        for line in txt.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    impl = part = None
+    for line in txt.splitlines():
+        if line.startswith("CPU implementer") and impl is None:
+            impl = line.split(":", 1)[1].strip()
+        if line.startswith("CPU part") and part is None:
+            part = line.split(":", 1)[1].strip()
+    return f"arm implementer {impl} part {part}" if impl else None
+
+
+def _oracle_one(inst, p, iters):
+    """Preparation (timed), then `iters` iterations (timed) of one instance."""
+    import dataclasses
+    from oracle import oracle as orc
+    q = dataclasses.replace(p, iterations=min(iters, p.iterations))
+    t0 = time.perf_counter()
+    o = orc.Oracle(inst, q)
+    t1 = time.perf_counter()
+    o.iterate(q.iterations)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, q.iterations
+
+
 def oracle_sample(insts, ps, count, iters):
-    """Times the CPU oracle on the first `count` instances for `iters` iterations."""
+    """Times the CPU oracle on the first `count` instances: preparation and
+    `iters` iterations separately, all instances concurrently (one thread
+    each, the C oracle releases the GIL), then the first instance alone on one
+    core.  The workload figure scales each instance's iteration time to its
+    full iteration count and adds its preparation once, as a step does."""
     import concurrent.futures as cf
     from oracle import oracle as orc
     orc.build()
-    import dataclasses
-    sub = [(insts[b], dataclasses.replace(ps[b], iterations=min(iters, ps[b].iterations)))
-           for b in range(min(count, len(insts)))]
+    sub = list(range(min(count, len(insts))))
     cores = min(len(sub), os.cpu_count() or 1)
-
-    def one(ip):
-        o = orc.Oracle(ip[0], ip[1])
-        o.iterate(ip[1].iterations)
-        return o.scalars()["L_gb"]
-
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=cores) as ex:      # the C oracle releases the GIL
-        list(ex.map(one, sub))
-    dt = time.perf_counter() - t0
-    steps = total_ant_steps([s[0] for s in sub], [s[1] for s in sub])
-    return steps / dt, dt, cores, len(sub), steps
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        res = list(ex.map(lambda b: _oracle_one(insts[b], ps[b], iters), sub))
+    wall = time.perf_counter() - t0
+    prep = [r[0] for r in res]
+    it_s = [r[1] for r in res]
+    done = [r[2] for r in res]
+    steps_sample = sum(ps[b].m * insts[b].n * done[q] for q, b in enumerate(sub))
+    full_steps = sum(ps[b].m * insts[b].n * ps[b].iterations for b in sub)
+    cpu_s_full = sum(prep[q] + it_s[q] * ps[b].iterations / max(done[q], 1) for q, b in enumerate(sub))
+    all_core = full_steps / (cpu_s_full / cores)
+    iter_rate = sum(ps[b].m * insts[b].n * done[q] for q, b in enumerate(sub)) / (sum(it_s) / cores)
+    p1, i1, d1 = _oracle_one(insts[0], ps[0], iters)          # one instance alone, one core
+    single = ps[0].m * insts[0].n * ps[0].iterations / (p1 + i1 * ps[0].iterations / max(d1, 1))
+    return {"value": all_core, "cores": cores, "instances": len(sub), "iters": iters,
+            "wall_s": wall, "ant_steps_sample": steps_sample,
+            "all_core": all_core, "single_core": single,
+            "iter_ant_steps_per_s": iter_rate,
+            "prep_s": sum(prep) / len(prep), "cpu_model": cpu_model()}
+
+
+def _cpu_block(c):
+    return {"value": c["value"], "unit": "ant-steps/s", "cores": c["cores"], "kind": "oracle",
+            "sample": (f"first {c['instances']} instances of the workload, preparation and {c['iters']} iterations "
+                       f"each timed separately on {c['cores']} threads ({c['ant_steps_sample']} ant-steps, "
+                       f"{c['wall_s']:.1f} s wall); value = the workload's ant-steps over its CPU time "
+                       f"(each instance's preparation once plus its iteration time scaled to its full "
+                       f"iteration count) divided by the threads used"),
+            "single_core": c["single_core"], "all_core": c["all_core"],
+            "iter_ant_steps_per_s": c["iter_ant_steps_per_s"], "prep_s": c["prep_s"],
+            "cpu_model": c["cpu_model"]}
 
 
 def run_reference(args):
@@ -241,23 +294,19 @@ def run_reference(args):
     else:
         insts, ps = workload(args.workload, 0)
     for _ in range(args.warmup):
-        oracle_sample(insts, ps, args.cpu_sample, 2)
-    vals, dts = [], []
-    for _ in range(args.steps):
-        v, dt, cores, cnt, steps = oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters)
-        vals.append(v)
-        dts.append(dt)
-    value = float(np.mean(vals))
-    sample = (f"first {cnt} instances of the workload, {args.cpu_iters} iterations each, "
-              f"preparation included, {steps} ant-steps per step")
+        oracle_sample(insts, ps, min(args.cpu_sample, 2), 1)
+    runs = [oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters) for _ in range(args.steps)]
+    value = float(np.mean([c["value"] for c in runs]))
+    dts = [c["wall_s"] for c in runs]
+    cpu = _cpu_block(runs[-1])
+    cpu["value"] = value
     print(json.dumps({
         "impl": "reference", "metric": "ant-steps/s", "value": value, "unit": "ant-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * float(np.mean(dts)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOAD_TEXT[args.workload]},
-        "cpu_baseline": {"value": value, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "ant-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -457,10 +506,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, cores, cnt, st = oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters)
-        cpu = {"value": v, "unit": "ant-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {cnt} instances of the workload, {args.cpu_iters} iterations each, "
-                         f"preparation included ({st} ant-steps, {dt:.1f} s wall)"}
+        cpu = _cpu_block(oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters))
 
     if rank == 0:
         line = {

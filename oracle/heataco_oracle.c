@@ -49,7 +49,8 @@ typedef struct {
     double alpha, beta, rho;
     double theta_h, eps, c_cap, q_level, p_best, logw_clip;
     int32_t degree_target;   /* d* of Sec. III-C: 2 symmetric, 1 ATSP */
-    int32_t local_search;    /* 0 none, 1 2-opt on the iteration-best tour, 2 on every ant's tour */
+    int32_t local_search;    /* 0 none; 2-opt: 1 on the iteration-best tour, 2 on every ant's tour;
+                                3-opt: 3 on the iteration-best tour, 4 on every ant's tour */
     int32_t baseline_scope;  /* 0 order statistic over C_i, 1 over the whole heatmap row */
     int32_t ls_k;            /* geometric neighbour-list size of the 2-opt */
     int32_t schedule;        /* 0: T+ = T_ib always; 1: MMAS u_gb schedule and restarts */
@@ -550,6 +551,195 @@ int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour
     return moves;
 }
 
+/* ------------------------------------------------------------ 3-opt (Sec. III-D)
+ *
+ * First-improvement 3-opt restricted to the geometric neighbour lists, with
+ * don't-look bits.  Reading (the paper names the operator only): a move is a
+ * sequential exchange in the notation of Lin and Kernighan.  For the examined
+ * city t2 = a and t1 = dir(a) (successor direction first), t3 runs over
+ * nbr(t2) while g1 = d(t1,t2) - d(t2,t3) > 0; for t4 = dir(t3) (then the
+ * other tour neighbour of t3): closing with (t4, t1) is the 2-opt move of the
+ * 2-opt above; otherwise t5 runs over nbr(t4) while g2 = g1 + d(t3,t4) -
+ * d(t4,t5) > 0 and t6 over (succ t5, pred t5).  Removed edges (t1,t2),
+ * (t3,t4), (t5,t6), added (t2,t3), (t4,t5), (t6,t1); a candidate counts when
+ * the result is one Hamiltonian cycle and its gain exceeds 1e-10.  Gains are
+ * FP64 in the order written: (g1 + d34) - d41 and ((g1 + d34) - d45 + d56)
+ * - d61.  The first such candidate in this order is applied; the bits of its
+ * cities are cleared and a is examined again; a city without a move gets its
+ * bit set.  Passes and rounds are those of the 2-opt above.
+ *
+ * Applying a move: the removed edges sit at tour positions e (edge between
+ * tour[e] and tour[e+1 mod n]); positions outside [e_min + 1, e_max] keep
+ * their cities, and the middle range is rewritten with the middle segments
+ * in the order and orientation the new cycle visits them when it leaves
+ * tour[e_min] (so the array changes only between the first and last removed
+ * edge). */
+
+typedef struct {
+    int r;          /* removed edges (2 or 3) */
+    int e[3];       /* their positions */
+    int seg[2];     /* middle segments in visiting order (index into the sorted edges) */
+    int rev[2];     /* 1: that segment is walked backwards */
+} orc_xchg;
+
+static int edge_pos(const int32_t *pos, int n, int u, int v)
+{
+    if (pos[v] == (pos[u] + 1) % n) return pos[u];
+    if (pos[u] == (pos[v] + 1) % n) return pos[v];
+    return -1;
+}
+
+/* The removed edges ed[k] (as city pairs) and the added edges given as pairs
+ * of (edge k, city); fills X when the exchange leaves one cycle. */
+static int orc_reconnect(const int32_t *tour, const int32_t *pos, int n, int r, const int (*ed)[2],
+                         const int (*add)[4], orc_xchg *X)
+{
+    int e[3], ord[3];
+    for (int k = 0; k < r; ++k) {
+        e[k] = edge_pos(pos, n, ed[k][0], ed[k][1]);
+        if (e[k] < 0) return 0;
+        ord[k] = k;
+    }
+    for (int a = 0; a < r; ++a)
+        for (int b = a + 1; b < r; ++b) if (e[a] == e[b]) return 0;
+    for (int a = 0; a < r; ++a)              /* sort by position */
+        for (int b = a + 1; b < r; ++b)
+            if (e[ord[b]] < e[ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
+    int rank[3];
+    for (int j = 0; j < r; ++j) rank[ord[j]] = j;
+    /* slot of a city on removed edge k: 2*j + side, j = position rank, side 0
+     * for tour[e] (end of the segment before the edge), 1 for tour[e+1] */
+    int partner[6];
+    for (int q = 0; q < 6; ++q) partner[q] = -1;
+    for (int a = 0; a < r; ++a) {
+        int sl[2];
+        for (int h = 0; h < 2; ++h) {
+            int k = add[a][2 * h], c = add[a][2 * h + 1];
+            int ek = e[k];
+            int side;
+            if (tour[ek] == c) side = 0;
+            else if (tour[(ek + 1) % n] == c) side = 1;
+            else return 0;
+            sl[h] = 2 * rank[k] + side;
+        }
+        if (partner[sl[0]] >= 0 || partner[sl[1]] >= 0 || sl[0] == sl[1]) return 0;
+        partner[sl[0]] = sl[1];
+        partner[sl[1]] = sl[0];
+    }
+    /* middle segment j (0 <= j < r-1) runs from slot 2j+1 (head) to slot
+     * 2(j+1) (tail); the fixed part ends at slot 0 and starts at slot 2r-1 */
+    int used[2] = {0, 0}, cnt = 0, cur = 0;
+    for (;;) {
+        int s = partner[cur];
+        if (s == 2 * r - 1) break;
+        if (s == 0) return 0;
+        int j, back;
+        if (s % 2 == 1) { j = (s - 1) / 2; back = 0; } else { j = s / 2 - 1; back = 1; }
+        if (j < 0 || j >= r - 1 || used[j] || cnt >= r - 1) return 0;
+        used[j] = 1;
+        X->seg[cnt] = j; X->rev[cnt] = back; ++cnt;
+        cur = back ? 2 * j + 1 : 2 * (j + 1);
+    }
+    if (cnt != r - 1) return 0;
+    X->r = r;
+    for (int j = 0; j < r; ++j) X->e[j] = e[ord[j]];
+    return 1;
+}
+
+static void orc_apply_xchg(int32_t *tour, int32_t *pos, int n, const orc_xchg *X, int32_t *tmp)
+{
+    int lo = X->e[0] + 1, w = 0;
+    for (int q = 0; q < X->r - 1; ++q) {
+        int j = X->seg[q];
+        int a = X->e[j] + 1, b = X->e[j + 1];      /* segment positions a..b */
+        if (!X->rev[q]) for (int p = a; p <= b; ++p) tmp[w++] = tour[p];
+        else for (int p = b; p >= a; --p) tmp[w++] = tour[p];
+    }
+    for (int q = 0; q < w; ++q) { tour[lo + q] = tmp[q]; pos[tmp[q]] = lo + q; }
+}
+
+int orc_three_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour)
+{
+    int n = in->n;
+    int32_t *pos = xcalloc((size_t)n, sizeof *pos);
+    int32_t *tmp = xcalloc((size_t)n, sizeof *tmp);
+    uint8_t *dlb = xcalloc((size_t)n, 1);
+    if (!pos || !dlb || !tmp) { free(pos); free(dlb); free(tmp); return ORC_ENOMEM; }
+    for (int p = 0; p < n; ++p) pos[tour[p]] = p;
+#define SUCC(c) tour[(pos[c] + 1) % n]
+#define PRED(c) tour[(pos[c] + n - 1) % n]
+    int moves = 0, round_moves;
+    const long long max_moves = 64LL * n + 1024;
+    do {
+      round_moves = 0;
+      memset(dlb, 0, (size_t)n);
+      int improved = 1;
+      while (improved && moves < max_moves) {
+        improved = 0;
+        for (int p = 0; p < n && moves < max_moves; ++p) {
+            int a = tour[p];
+            if (dlb[a]) continue;
+            int moved;
+            do {
+                moved = 0;
+                for (int dir = 0; dir < 2 && !moved; ++dir) {
+                    int t2 = a, t1 = dir == 0 ? SUCC(a) : PRED(a);
+                    double d12 = orc_dist(in, t1, t2);
+                    for (int q = 0; q < K && !moved; ++q) {
+                        int t3 = nbr[(int64_t)a * K + q];
+                        double g1 = d12 - orc_dist(in, t2, t3);
+                        if (g1 <= 0.0) break;
+                        for (int c4 = 0; c4 < 2 && !moved; ++c4) {
+                            int t4 = (c4 == 0) == (dir == 0) ? SUCC(t3) : PRED(t3);
+                            if ((t3 == t1 && t4 == t2) || (t3 == t2 && t4 == t1)) continue;
+                            double d34 = orc_dist(in, t3, t4);
+                            orc_xchg X;
+                            if (c4 == 0 && t4 != t1) {
+                                double gain = (g1 + d34) - orc_dist(in, t4, t1);
+                                int ed[2][2] = {{t1, t2}, {t3, t4}};
+                                int add[2][4] = {{0, t2, 1, t3}, {1, t4, 0, t1}};
+                                if (gain > ORC_LS_GAIN && orc_reconnect(tour, pos, n, 2, ed, add, &X)) {
+                                    orc_apply_xchg(tour, pos, n, &X, tmp);
+                                    dlb[t1] = dlb[t2] = dlb[t3] = dlb[t4] = 0;
+                                    moved = 1;
+                                    break;
+                                }
+                            }
+                            double g1b = g1 + d34;
+                            for (int r = 0; r < K && !moved; ++r) {
+                                int t5 = nbr[(int64_t)t4 * K + r];
+                                double g2 = g1b - orc_dist(in, t4, t5);
+                                if (g2 <= 0.0) break;
+                                if (t5 == t3) continue;
+                                for (int c6 = 0; c6 < 2; ++c6) {
+                                    int t6 = c6 == 0 ? SUCC(t5) : PRED(t5);
+                                    if (t6 == t1) continue;
+                                    double gain = (g2 + orc_dist(in, t5, t6)) - orc_dist(in, t6, t1);
+                                    if (!(gain > ORC_LS_GAIN)) continue;
+                                    int ed[3][2] = {{t1, t2}, {t3, t4}, {t5, t6}};
+                                    int add[3][4] = {{0, t2, 1, t3}, {1, t4, 2, t5}, {2, t6, 0, t1}};
+                                    if (!orc_reconnect(tour, pos, n, 3, ed, add, &X)) continue;
+                                    orc_apply_xchg(tour, pos, n, &X, tmp);
+                                    dlb[t1] = dlb[t2] = dlb[t3] = dlb[t4] = dlb[t5] = dlb[t6] = 0;
+                                    moved = 1;
+                                    break;
+                                }
+                            }
+                        }
+                    }
+                }
+                if (moved) { improved = 1; ++moves; ++round_moves; }
+            } while (moved && moves < max_moves);
+            dlb[a] = 1;
+        }
+      }
+    } while (round_moves > 0 && moves < max_moves);
+#undef SUCC
+#undef PRED
+    free(pos); free(dlb); free(tmp);
+    return moves;
+}
+
 /* ------------------------------------------------------------ tour length */
 
 /* Eq. (tour_length) in FP64.  Reading: the paper fixes no summation order.
@@ -594,7 +784,8 @@ static void nn_tour(orc_state *S)
         S->nn_tour[s] = j;
         S->visited[j] = 1;
     }
-    if (S->p.local_search) orc_two_opt(&S->in, S->nbr, S->ls_k, S->nn_tour);
+    if (S->p.local_search == 1 || S->p.local_search == 2) orc_two_opt(&S->in, S->nbr, S->ls_k, S->nn_tour);
+    if (S->p.local_search >= 3) orc_three_opt(&S->in, S->nbr, S->ls_k, S->nn_tour);
     S->L_nn = orc_tour_length(&S->in, S->nn_tour);
 }
 
@@ -746,17 +937,19 @@ static void iterate_once(orc_state *S)
 {
     int n = S->n, m = S->p.m, kp = S->k_pad;
     for (int a = 0; a < m; ++a) construct(S, a, S->tours + (int64_t)a * n, &S->lens[a]);
-    if (S->p.local_search == 2)                          /* Algorithm 1: local search on every ant */
+    if (S->p.local_search == 2 || S->p.local_search == 4)   /* Algorithm 1: local search on every ant */
         for (int a = 0; a < m; ++a) {
-            orc_two_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
+            if (S->p.local_search == 2) orc_two_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
+            else orc_three_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
             S->lens[a] = orc_tour_length(&S->in, S->tours + (int64_t)a * n);
         }
     int ib = 0;                                          /* iteration best, ties -> lowest ant */
     for (int a = 1; a < m; ++a) if (S->lens[a] < S->lens[ib]) ib = a;
     memcpy(S->ib_tour, S->tours + (int64_t)ib * n, (size_t)n * sizeof(int32_t));
     S->L_ib = S->lens[ib];
-    if (S->p.local_search == 1) {                        /* 2-opt on T_ib before it is used */
-        orc_two_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
+    if (S->p.local_search == 1 || S->p.local_search == 3) {   /* local search on T_ib before it is used */
+        if (S->p.local_search == 1) orc_two_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
+        else orc_three_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
         S->L_ib = orc_tour_length(&S->in, S->ib_tour);
     }
     const int32_t t1 = S->t + 1;                         /* this iteration, counted from 1 */
@@ -846,7 +1039,7 @@ static int check_inputs(const orc_instance *in, const orc_params *p)
     if (p->rho <= 0.0 || p->rho >= 1.0 || p->degree_target < 1) return ORC_EINVAL;
     if (p->schedule != 0 && p->schedule != 1) return ORC_EINVAL;
     if (p->kappa_mode < 0 || p->kappa_mode > 2) return ORC_EINVAL;
-    if (p->local_search < 0 || p->local_search > 2) return ORC_EINVAL;
+    if (p->local_search < 0 || p->local_search > 4) return ORC_EINVAL;
     if (p->local_search && (in->kind != 0 || p->ls_k < 1 || p->ls_k > in->n - 1)) return ORC_EINVAL;
     /* the 2-opt's FP32 pre-test needs finite squared coordinate differences:
      * |x|, |y| <= 1e18 with local search (the CUDA path checks the same) */

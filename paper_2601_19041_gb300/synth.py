@@ -181,6 +181,54 @@ def atsp_instance(seed: int, n: int, K: int = 50, noise_hi: float = 0.5) -> Inst
                     symmetrize=0, seed=seed, meta={"family": "atsp", "knn": K})
 
 
+def softdist_heatmap(pts: np.ndarray, t_rel: float = 1.0, floor: float = 1e-6, k_max: int = 64,
+                     dtype=np.float32, chunk: int = 1024):
+    """SoftDist heatmap (the non-learned control of Sec. V-C): row i is the
+    softmax of the negated distances, H_ij = exp(-d_ij/T) / sum_{l != i}
+    exp(-d_il/T), over all j != i.  The paper does not state the temperature;
+    here T = t_rel times the instance's mean nearest-neighbour distance, a
+    documented parameter.  Entries below ``floor`` (far under the decoder's
+    threshold theta_h = 1e-4) are not stored, and at most the ``k_max``
+    largest of a row are kept.  Returns CSR (rowptr, col, val)."""
+    p = pts.astype(np.float64)
+    n = len(p)
+    nn, nd = knn_euclid(pts, 1)
+    T = max(t_rel * float(nd.mean()), 1e-300)
+    K = min(k_max, n - 1)
+    rows_c, rows_v = [], []
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        dx = p[s:e, 0:1] - p[None, :, 0]
+        dy = p[s:e, 1:2] - p[None, :, 1]
+        d = np.sqrt(dx * dx + dy * dy)
+        d[np.arange(e - s), np.arange(s, e)] = np.inf          # j != i
+        z = -(d - d.min(axis=1, keepdims=True)) / T             # shifted for a stable softmax
+        w = np.exp(z)
+        w /= w.sum(axis=1, keepdims=True)
+        top = np.argpartition(-w, K - 1, axis=1)[:, :K]
+        for r in range(e - s):
+            js = top[r][w[r, top[r]] >= floor]
+            js.sort()
+            rows_c.append(js.astype(np.int32))
+            rows_v.append(w[r, js].astype(dtype))
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum([len(c) for c in rows_c])
+    return (rowptr.astype(np.int32), np.concatenate(rows_c) if rows_c else np.zeros(0, np.int32),
+            np.concatenate(rows_v) if rows_v else np.zeros(0, dtype))
+
+
+def softdist_instance(seed: int, n: int, t_rel: float = 1.0, family: str = "uniform",
+                      symmetrize: int = 1) -> Instance:
+    """Uniform (or other family) points with a SoftDist heatmap."""
+    rng = np.random.default_rng(seed)
+    pts = {"uniform": uniform_points, "gmm": gaussian_mixture_points,
+           "grid": perturbed_grid_points}[family](rng, n)
+    rowptr, col, val = softdist_heatmap(pts, t_rel)
+    return Instance(n=n, kind=0, coords=pts, cost=None, rowptr=rowptr, col=col, val=val,
+                    symmetrize=symmetrize, seed=seed, meta={"family": family, "heatmap": "softdist",
+                                                            "t_rel": t_rel})
+
+
 def empty_heatmap(n: int):
     return np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32)
 

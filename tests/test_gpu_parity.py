@@ -111,6 +111,8 @@ CASES = {
     # the ablation variants of Sec. V-D: fixed kappa = 1, and kappa without the cap factor
     "kappa_fixed_one": lambda: (synth.euclid_instance(29, 240, K=50), params(m=12, k=20, iterations=7, rho=0.2, seed=25, kappa_mode=1)),
     "kappa_no_cap": lambda: (synth.euclid_instance(30, 260, K=50), params(m=12, k=20, iterations=7, rho=0.2, seed=26, kappa_mode=2)),
+    # the SoftDist control heatmap (Sec. V-C): a softmax of negated distances
+    "softdist": lambda: (synth.softdist_instance(32, 280), params(m=12, k=20, iterations=7, rho=0.2, seed=27)),
     "clustered": lambda: (synth.euclid_instance(25, 300, K=50, family="gmm"), params(m=12, k=20, iterations=6, rho=0.2, seed=19)),
     "grid": lambda: (synth.euclid_instance(26, 289, K=50, family="grid"), params(m=12, k=20, iterations=6, rho=0.2, seed=20)),
 }
