@@ -90,9 +90,12 @@ typedef struct {
  *                   neighbour lists and don't-look bits (Sec. III-D) on the
  *                   iteration-best tour and on T_NN; 2 the same 2-opt on
  *                   every ant's tour right after its construction (the
- *                   local search of Algorithm 1) and on T_NN; tau_min =
- *                   tau_max/(2n) for both.
- *                   Mode 2 is not available with 32 ants per warp
+ *                   local search of Algorithm 1) and on T_NN; 3 and 4 the
+ *                   same with first-improvement 3-opt (sequential exchanges
+ *                   of up to three edges, neighbour lists, don't-look bits)
+ *                   instead of 2-opt; tau_min = tau_max/(2n) for all.
+ *                   Local search needs kind 0 and |x|, |y| <= 1e18.
+ *                   Modes 2 and 4 are not available with 32 ants per warp
  *                   (HAC_EUNSUPPORTED).
  *   baseline_scope  0: order statistic b_i over the candidates C_i; 1: over all
  *                   heatmap entries of row i (eq. background defines c on C_i

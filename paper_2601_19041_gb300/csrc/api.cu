@@ -39,7 +39,7 @@ struct hac_batch {
     int *d_err = nullptr;
     int max_n = 0, max_kp = 0;
     bool any_ls = false;
-    int ls_all_m = 0;               // largest m among the instances with 2-opt on every ant
+    int ls_all_m = 0;               // largest m among the instances with local search on every ant
     std::vector<int> t_host;
     cudaGraphExec_t gexec = nullptr;
     int graph_kernels = 0;          // kernels inside one graph replay
@@ -150,7 +150,7 @@ static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params 
         bt->max_n = std::max(bt->max_n, z.n);
         bt->max_kp = std::max(bt->max_kp, z.kp);
         bt->any_ls |= z.ls != 0;
-        if (z.ls == 2) bt->ls_all_m = std::max(bt->ls_all_m, z.m);
+        if (z.ls == 2 || z.ls == 4) bt->ls_all_m = std::max(bt->ls_all_m, z.m);
     }
     // work tables
     std::vector<int2> rowmap, slotmap;
@@ -278,7 +278,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
     if (ex.ants_per_warp == 32)   // step-major tours: 2-opt on every ant needs them ant by ant
         for (int b = 0; b < count; ++b)
-            if (ps[b].local_search == 2) return HAC_EUNSUPPORTED;
+            if (ps[b].local_search == 2 || ps[b].local_search == 4) return HAC_EUNSUPPORTED;
 
     hac_batch *bt = new (std::nothrow) hac_batch;
     if (!bt) return HAC_ENOMEM;

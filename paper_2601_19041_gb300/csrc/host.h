@@ -62,7 +62,7 @@ inline int check_params(const hac_instance &in, const hac_params &p)
     if (p.baseline_scope != 0 && p.baseline_scope != 1) return HAC_EINVAL;
     if (p.schedule != 0 && p.schedule != 1) return HAC_EINVAL;
     if (p.kappa_mode < 0 || p.kappa_mode > 2) return HAC_EINVAL;
-    if (p.local_search < 0 || p.local_search > 2) return HAC_EINVAL;
+    if (p.local_search < 0 || p.local_search > 4) return HAC_EINVAL;
     if (p.local_search) {
         if (in.kind != 0) return HAC_EUNSUPPORTED;
         if (p.ls_k < 1 || p.ls_k > 32 || p.ls_k > in.n - 1) return HAC_EINVAL;
@@ -169,7 +169,7 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
         put("ls_pos", A.take(n * 4));
         put("ls_el", A.take(n * 4));
         put("ls_dlb", A.take(n));
-        if (z.ls == 2) {   // every ant's 2-opt: its own positions, edge lengths, bits
+        if (z.ls == 2 || z.ls == 4) {   // every ant's local search: its own positions, scratch, bits
             put("lsa_pos", A.take((size_t)z.m * n * 4));
             put("lsa_el", A.take((size_t)z.m * n * 4));
             put("lsa_dlb", A.take((size_t)z.m * n));

@@ -319,7 +319,7 @@ int enqueue_step_route(hac_server *sv, const std::vector<int> &mem, int par)
         max_n = std::max(max_n, S.z.n);
         max_kp = std::max(max_kp, S.z.kp);
         any_ls |= S.z.ls != 0;
-        if (S.z.ls == 2) ls_all_m = std::max(ls_all_m, S.z.m);
+        if (S.z.ls == 2 || S.z.ls == 4) ls_all_m = std::max(ls_all_m, S.z.m);
     }
     const int count = (int)mem.size();
     cudaStream_t ss = sv->sstream;
@@ -469,7 +469,7 @@ int hac_server_submit(hac_server *sv, const hac_instance *in, const hac_params *
     if ((st = check_host_data(*in, *p))) return st;
     const int route = sv->cfg.step_min_n > 0 && z.n >= sv->cfg.step_min_n ? 1 : 0;
     if (!route && (st = fits_fused(sv, z))) return st;
-    if (!route && sv->ex.ants_per_warp == 32 && z.ls == 2) return HAC_EUNSUPPORTED;   // step-major tours
+    if (!route && sv->ex.ants_per_warp == 32 && (z.ls == 2 || z.ls == 4)) return HAC_EUNSUPPORTED;   // step-major tours
     int q = 0;
     while (q < sv->cfg.max_slots && sv->slots[q].state != R_FREE) ++q;
     if (q == sv->cfg.max_slots) return HAC_EBUSY;

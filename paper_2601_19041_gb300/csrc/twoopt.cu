@@ -1,6 +1,7 @@
-// 2-opt kernels (one warp per instance, its arrays in shared memory when they
-// fit); the search itself is in twoopt.cuh.
-#include "twoopt.cuh"
+// Local-search kernels (one warp per tour, its arrays in shared memory when
+// they fit): 2-opt (local_search 1 and 2, twoopt.cuh) or 3-opt (3 and 4,
+// threeopt.cuh).
+#include "threeopt.cuh"
 
 namespace hac {
 
@@ -9,7 +10,9 @@ __global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
     extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x];
     if (!I.local_search) return;
-    warp_two_opt(I, I.nn_tour, ls_shared(I, I.nn_tour, ls_sm, smem_bytes, ls_global(I, I.nn_tour)));
+    const LsMem M = ls_shared(I, I.nn_tour, ls_sm, smem_bytes, ls_global(I, I.nn_tour));
+    if (I.local_search >= 3) warp_three_opt(I, I.nn_tour, M);
+    else warp_two_opt(I, I.nn_tour, M);
     const double L = warp_tour_length(I, I.nn_tour);
     if (threadIdx.x == 0) I.st->L_nn = L;
 }
@@ -18,22 +21,26 @@ __global__ void k_two_opt_ib(const DevInst *insts, unsigned smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x];
-    if (I.local_search != 1 || !I.st->active) return;
-    warp_two_opt(I, I.ib_tour, ls_shared(I, I.ib_tour, ls_sm, smem_bytes, ls_global(I, I.ib_tour)));
+    if ((I.local_search != 1 && I.local_search != 3) || !I.st->active) return;
+    const LsMem M = ls_shared(I, I.ib_tour, ls_sm, smem_bytes, ls_global(I, I.ib_tour));
+    if (I.local_search == 3) warp_three_opt(I, I.ib_tour, M);
+    else warp_two_opt(I, I.ib_tour, M);
     const double L = warp_tour_length(I, I.ib_tour);
     if (threadIdx.x == 0) I.st->L_ib = L;
 }
 
-// local_search = 2 (Algorithm 1's local search on every ant): ant blockIdx.x % max_m of instance
+// local_search = 2 or 4 (Algorithm 1's local search on every ant): ant blockIdx.x % max_m of instance
 // blockIdx.x / max_m, right after construction; its length is recomputed
 __global__ void k_two_opt_all(const DevInst *insts, int max_m, unsigned smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char ls_sm[];
     const DevInst &I = insts[blockIdx.x / max_m];
     const int a = blockIdx.x % max_m;
-    if (I.local_search != 2 || a >= I.m || I.st->t >= I.iters) return;
+    if ((I.local_search != 2 && I.local_search != 4) || a >= I.m || I.st->t >= I.iters) return;
     int32_t *tour = I.tours + (size_t)a * I.n;
-    warp_two_opt(I, tour, ls_shared(I, tour, ls_sm, smem_bytes, ls_ant(I, a)));
+    const LsMem M = ls_shared(I, tour, ls_sm, smem_bytes, ls_ant(I, a));
+    if (I.local_search == 4) warp_three_opt(I, tour, M);
+    else warp_two_opt(I, tour, M);
     const double L = warp_tour_length(I, tour);
     if (threadIdx.x == 0) I.lens[a] = L;
 }

@@ -113,6 +113,11 @@ CASES = {
     "kappa_no_cap": lambda: (synth.euclid_instance(30, 260, K=50), params(m=12, k=20, iterations=7, rho=0.2, seed=26, kappa_mode=2)),
     # the SoftDist control heatmap (Sec. V-C): a softmax of negated distances
     "softdist": lambda: (synth.softdist_instance(32, 280), params(m=12, k=20, iterations=7, rho=0.2, seed=27)),
+    # 3-opt (Sec. III-D) on T_ib and T_NN; on every ant
+    "three_opt": lambda: (synth.euclid_instance(33, 260, K=10), params(m=10, k=10, iterations=6, rho=0.2, local_search=3, seed=28)),
+    "three_opt_grid": lambda: (euclid(np.stack(np.meshgrid(np.arange(13), np.arange(13)), -1).reshape(-1, 2) / 12.0),
+                               params(m=8, k=10, iterations=5, rho=0.2, local_search=3, ls_k=9, seed=29)),
+    "three_opt_every_ant": lambda: (synth.euclid_instance(34, 140, K=10), params(m=7, k=10, iterations=4, rho=0.2, local_search=4, ls_k=12, seed=30)),
     "clustered": lambda: (synth.euclid_instance(25, 300, K=50, family="gmm"), params(m=12, k=20, iterations=6, rho=0.2, seed=19)),
     "grid": lambda: (synth.euclid_instance(26, 289, K=50, family="grid"), params(m=12, k=20, iterations=6, rho=0.2, seed=20)),
 }
@@ -140,9 +145,11 @@ FUSED = [dict(apw=2, clog=0, fbl=32), dict(apw=4, clog=1, fbl=0), dict(apw=4, cl
 @pytest.mark.parametrize("cfg", FUSED, ids=lambda c: f"apw{c['apw']}_C{1 << c['clog']}_fbl{c['fbl']}")
 @pytest.mark.parametrize("name", ["sym50nn_k20", "sym10nn_k10_ragged", "k32", "k7_pad", "n3",
                                   "empty_heatmap", "atsp", "two_opt", "two_opt_grid", "alpha_beta_powers",
-                                  "kappa_no_cap"])
+                                  "kappa_no_cap", "three_opt", "three_opt_every_ant"])
 def test_fused_kernel_parity(hac, orc, name, cfg):
     inst, p = CASES[name]()
+    if cfg["apw"] == 32 and p.local_search in (2, 4):
+        pytest.skip("local search on every ant needs ant-major tours")
     ex = hac.make_exec(cfg["apw"], 0, 1, fused=1, fallback_list=cfg["fbl"], cluster_log2=cfg["clog"])
     run_case(hac, orc, [inst], [p], exec_=ex)
 
