@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--step-min-n", type=int, default=3000,
                     help="serve: requests with n >= this run on the per-step kernels (0: cluster kernel only)")
     ap.add_argument("--step-apw", type=int, default=1, help="serve: ants per warp of the per-step route")
+    ap.add_argument("--plain-requests", type=int, default=24,
+                    help="serve: requests of the stream served one at a time for the plain-GPU comparison")
     return ap.parse_args()
 
 
@@ -442,6 +444,42 @@ def run_ours(args):
     construct_share = stats["construct_ms"] / dev_ms if dev_ms else None
     kernel_name = "k_fused (construct + update, all iterations)" if args.fused else "k_construct"
 
+    # latency model: a batch cannot finish before its longest instance, whose
+    # iterations are n sequential construction steps each.  Decode that
+    # instance alone in the same layout (untimed for `value`), and express its
+    # step in ns and in SM cycles at the median clock seen in the timed region.
+    latency = None
+    if rank == 0:
+        crit = max(range(count), key=lambda b: ps[b].m * insts[b].n * ps[b].iterations)
+        mc = heataco._Marshal([dins[crit]], [ps[crit]], True)
+        exc = heataco.make_exec(args.apw, args.wpb, use_graph=1, fused=args.fused, fallback_list=args.fbl,
+                                cluster_log2=args.clog)
+        crit_ms = []
+        for rep in range(2):
+            h = C.c_void_p()
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            heataco._check(L.hac_batch_create(mc.ins, mc.ps, 1, 1, C.c_void_p(ws.data_ptr()), ws_bytes,
+                                              C.byref(exc), C.c_void_p(stream.cuda_stream), C.byref(h)), "create")
+            heataco._check(L.hac_batch_sync(h), "sync")
+            a0.record(stream)
+            heataco._check(L.hac_batch_run(h), "run")
+            a1.record(stream)
+            heataco._check(L.hac_batch_sync(h), "sync")
+            L.hac_batch_destroy(h)
+            crit_ms.append(a0.elapsed_time(a1))
+        cms = min(crit_ms)
+        steps_crit = insts[crit].n * ps[crit].iterations
+        step_ns = cms * 1e6 / steps_crit
+        mhz = clk.get("sm_mhz") or None
+        latency = {"critical_instance": {"n": insts[crit].n, "m": ps[crit].m, "iterations": ps[crit].iterations},
+                   "critical_path_ms": cms, "batch_ms": t_max / args.steps,
+                   "critical_share": cms / (t_max / args.steps),
+                   "step_ns": step_ns, "step_cycles": step_ns * mhz / 1000.0 if mhz else None,
+                   "note": "the longest instance decoded alone in the same layout (its iterations only); "
+                           "a batch cannot finish before it, so value <= ant-steps per step / critical path"}
+
     # the comparator: plain GPU MMAS, one instance per launch sequence
     # (per-iteration kernels, CUDA graphs), on a sample of the same instances
     plain = None
@@ -519,17 +557,19 @@ def run_ours(args):
                        "parallelism": f"instance batches, one per GPU ({world})",
                        "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
                        "inputs": "resident in HBM before the timed region",
-                       "ants_per_warp": ex.ants_per_warp or 4, "fused": args.fused,
+                       "ants_per_warp": (ex.ants_per_warp or ("per instance: 4 on one CTA, else 2 on a cluster"
+                                                               if args.fused else 4)), "fused": args.fused,
                        "warps_per_block": args.wpb, "cluster_log2": args.clog,
                        "fallback_list": args.fbl, "autotune": tune,
                        "kernel_timing": "CUDA events per launch"},
             "instances_per_s": inst_per_s,
             "e2e": e2e,
             "plain_gpu": plain,
+            "latency_model": latency,
             "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                         "traffic": NCU_TRAFFIC.get((args.workload, args.fused, ex.ants_per_warp or 4, args.fbl,
+                         "traffic": NCU_TRAFFIC.get((args.workload, args.fused, ex.ants_per_warp, args.fbl,
                                                      args.clog, ps[0].iterations)) if count == 128 else None,
                          "algorithmic_bytes_per_launch": per_launch_bytes,
                          "avg_launch_ms": avg_ms, "share_of_step": construct_share},
@@ -645,36 +685,34 @@ def run_serve(args):
     for q, r in enumerate(reqs):
         by_n.setdefault(r.inst.n, []).append(lat[q])
 
-    # plain GPU: one request at a time (per-iteration kernels, CUDA graphs),
-    # FIFO on the same arrivals; service time per size class measured on GPU
+    # plain GPU, measured: the first requests of the same stream served one at
+    # a time in arrival order (FIFO), each decoded alone by hac_solve_batch with
+    # the per-iteration kernels and CUDA graphs, against the wall clock with
+    # the stream's own arrival times; the server's latencies on the same
+    # requests are reported beside them
     plain = None
     if args.plain_sample:
-        stream = torch.cuda.Stream()
+        P = min(len(reqs), max(1, args.plain_requests))
         exp = heataco.make_exec(2, 8, use_graph=1, fused=0, fallback_list=0)
-        per_iter, fixed = {}, {}
-        for n in sorted(by_n):
-            q = next(r for r in reqs if r.inst.n == n)
-            ts = []
-            for it in (20, 60):
-                p = synth.Params(**{**q.params.__dict__, "iterations": it})
-                torch.cuda.synchronize()
-                a = time.perf_counter()
-                heataco.solve_batch([q.inst], [p], exp)
-                ts.append(time.perf_counter() - a)
-            per_iter[n] = max(0.0, (ts[1] - ts[0]) / 40.0)
-            fixed[n] = max(0.0, ts[0] - 20 * per_iter[n])
-        free_at, plat = 0.0, []
-        for r in reqs:
-            s = fixed[r.inst.n] + per_iter[r.inst.n] * r.params.iterations
-            start = max(free_at, r.arrival)
-            free_at = start + s
-            plat.append(1000.0 * (free_at - r.arrival))
-        plain = {"p50_ms": pct(plat, 50), "p99_ms": pct(plat, 99),
-                 "instances_per_s": len(reqs) / (free_at - reqs[0].arrival),
-                 "method": "FIFO queue simulated on the same arrivals with per-size service times "
-                           "(fixed + per-iteration) measured on this GPU by decoding one request "
-                           "alone at 20 and 60 iterations",
-                 "service_ms_at_200_iters": {str(n): 1000.0 * (fixed[n] + 200 * per_iter[n]) for n in per_iter}}
+        warm = reqs[0]
+        heataco.solve_batch([warm.inst], [synth.Params(**{**warm.params.__dict__, "iterations": 2})], exp)
+        torch.cuda.synchronize()
+        t0p = time.perf_counter()
+        plat, srv_lat = [], []
+        for q in range(P):
+            now = time.perf_counter() - t0p
+            arr = reqs[q].arrival - reqs[0].arrival
+            if arr > now:
+                time.sleep(arr - now)
+            heataco.solve_batch([reqs[q].inst], [reqs[q].params], exp)
+            plat.append(1000.0 * (time.perf_counter() - t0p - arr))
+            srv_lat.append(lat[q])
+        span_p = time.perf_counter() - t0p
+        plain = {"requests": P, "p50_ms": pct(plat, 50), "p99_ms": pct(plat, 99),
+                 "instances_per_s": P / span_p,
+                 "server_p50_ms_same_requests": pct(srv_lat, 50), "server_p99_ms_same_requests": pct(srv_lat, 99),
+                 "method": "measured: the first requests of the stream decoded one at a time (FIFO) at their "
+                           "arrival times by hac_solve_batch (per-iteration kernels, CUDA graphs)"}
 
     value = len(reqs) / span
     line = {

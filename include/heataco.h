@@ -48,7 +48,7 @@ enum hac_status {
     HAC_ENOMEM = -2,        /* workspace too small, or host allocation failed */
     HAC_ECUDA = -3,         /* a CUDA runtime call failed (see hac_last_cuda_error) */
     HAC_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
-    HAC_EUNSUPPORTED = -5,  /* combination not supported (e.g. 2-opt on an ATSP) */
+    HAC_EUNSUPPORTED = -5,  /* combination not supported (e.g. 3-opt on an ATSP) */
     HAC_EBUSY = -6          /* serving: request not finished yet / no slot free */
 };
 
@@ -94,7 +94,12 @@ typedef struct {
  *                   same with first-improvement 3-opt (sequential exchanges
  *                   of up to three edges, neighbour lists, don't-look bits)
  *                   instead of 2-opt; tau_min = tau_max/(2n) for all.
- *                   Local search needs kind 0 and |x|, |y| <= 1e18.
+ *                   With kind 1 (ATSP), modes 1 and 2 run the directed 2-opt
+ *                   (the 2-opt move that reverses a path, its gain counting
+ *                   the path's backward minus forward arc costs; the paper's
+ *                   Jonker-Volgenant based 2-opt) and modes 3 and 4 are
+ *                   HAC_EUNSUPPORTED.  With kind 0 local search needs
+ *                   |x|, |y| <= 1e18.
  *                   Modes 2 and 4 are not available with 32 ants per warp
  *                   (HAC_EUNSUPPORTED).
  *   baseline_scope  0: order statistic b_i over the candidates C_i; 1: over all

@@ -551,6 +551,97 @@ int orc_two_opt(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour
     return moves;
 }
 
+/* ----------------------------------------- directed 2-opt for the ATSP (Sec. III-D)
+ *
+ * Reading (the paper names a directed 2-opt based on the Jonker-Volgenant
+ * reduction): in the 2n-node symmetric graph of that reduction every city is
+ * a pair (in-copy, out-copy) joined by a fixed edge, and an ATSP tour is a
+ * symmetric tour that alternates the copies.  The 2-opt move that reverses
+ * a run of whole pairs keeps every fixed edge and turns the arcs of the run
+ * around; in the directed tour it removes two arcs, adds two arcs and
+ * reverses the path between them, whose cost changes from its forward sum F
+ * to its backward sum R.  The search is that of the 2-opt above with arc
+ * costs: for the examined city a,
+ *   successor side: a+ = succ(a), b over nbr(a) (smallest c(a, b)) while
+ *     g1 = c(a, a+) - c(a, b) > 0 (b = a+ or succ(b) = a skipped); remove
+ *     (a, a+), (b, b+), add (a, b), (a+, b+), reverse the path a+ .. b;
+ *     gain = (((g1 + c(b, b+)) - c(a+, b+)) + F) - R;
+ *   predecessor side: a- = pred(a), b over nbr(a) while g1 = c(a-, a) -
+ *     c(a, b) > 0 (b = a- or pred(b) = a skipped); remove (a-, a), (b-, b),
+ *     add (a-, b-), (a, b), reverse the path a .. b-;
+ *     gain = (((g1 + c(b-, b)) - c(a-, b-)) + F) - R.
+ * F and R sum the path's arcs in the order of the tour length (arc k of the
+ * path into partial k mod 32, then the pairwise tree).  The path is always
+ * reversed in place (its complement would reverse the tour's direction). */
+
+static double path_cost(const orc_instance *in, const int32_t *tour, int n, int i, int len, int backward)
+{
+    double P[32];
+    for (int q = 0; q < 32; ++q) P[q] = 0.0;
+    for (int k = 0; k + 1 < len; ++k) {
+        int u = tour[(i + k) % n], v = tour[(i + k + 1) % n];
+        P[k % 32] = P[k % 32] + (backward ? orc_dist(in, v, u) : orc_dist(in, u, v));
+    }
+    for (int w = 1; w < 32; w *= 2)
+        for (int q = 0; q < 32; q += 2 * w) P[q] = P[q] + P[q + w];
+    return P[0];
+}
+
+int orc_two_opt_directed(const orc_instance *in, const int32_t *nbr, int K, int32_t *tour)
+{
+    int n = in->n;
+    int32_t *pos = xcalloc((size_t)n, sizeof *pos);
+    uint8_t *dlb = xcalloc((size_t)n, 1);
+    if (!pos || !dlb) { free(pos); free(dlb); return ORC_ENOMEM; }
+    for (int p = 0; p < n; ++p) pos[tour[p]] = p;
+    int moves = 0, round_moves;
+    const long long max_moves = 64LL * n + 1024;
+    do {
+      round_moves = 0;
+      memset(dlb, 0, (size_t)n);
+      int improved = 1;
+      while (improved && moves < max_moves) {
+        improved = 0;
+        for (int p = 0; p < n && moves < max_moves; ++p) {
+            int a = tour[p];
+            if (dlb[a]) continue;
+            int moved;
+            do {
+                moved = 0;
+                for (int dir = 0; dir < 2 && !moved; ++dir) {
+                    int x = dir == 0 ? tour[(pos[a] + 1) % n] : tour[(pos[a] + n - 1) % n];   /* a+ or a- */
+                    double cx = dir == 0 ? orc_dist(in, a, x) : orc_dist(in, x, a);
+                    for (int q = 0; q < K; ++q) {
+                        int b = nbr[(int64_t)a * K + q];
+                        double g1 = cx - orc_dist(in, a, b);
+                        if (g1 <= 0.0) break;
+                        int y = dir == 0 ? tour[(pos[b] + 1) % n] : tour[(pos[b] + n - 1) % n];  /* b+ or b- */
+                        if (b == x || y == a) continue;
+                        int i0 = dir == 0 ? pos[x] : pos[a];          /* path start */
+                        int i1 = dir == 0 ? pos[b] : pos[y];          /* path end */
+                        int len = (i1 - i0 + n) % n + 1;
+                        double F = path_cost(in, tour, n, i0, len, 0);
+                        double R = path_cost(in, tour, n, i0, len, 1);
+                        double gain = dir == 0
+                            ? (((g1 + orc_dist(in, b, y)) - orc_dist(in, x, y)) + F) - R
+                            : (((g1 + orc_dist(in, y, b)) - orc_dist(in, x, y)) + F) - R;
+                        if (gain > ORC_LS_GAIN) {
+                            reverse_cyclic(tour, pos, n, i0, len);
+                            dlb[a] = dlb[x] = dlb[b] = dlb[y] = 0;
+                            moved = 1; improved = 1; ++moves; ++round_moves;
+                            break;
+                        }
+                    }
+                }
+            } while (moved && moves < max_moves);
+            dlb[a] = 1;
+        }
+      }
+    } while (round_moves > 0 && moves < max_moves);
+    free(pos); free(dlb);
+    return moves;
+}
+
 /* ------------------------------------------------------------ 3-opt (Sec. III-D)
  *
  * First-improvement 3-opt restricted to the geometric neighbour lists, with
@@ -772,6 +863,13 @@ static int nearest_unvisited(const orc_instance *in, const uint8_t *vis, int i)
     return best;
 }
 
+/* 2-opt of the instance's kind: symmetric, or directed for the ATSP. */
+static void orc_local_2opt(orc_state *S, int32_t *tour)
+{
+    if (S->in.kind == 1) orc_two_opt_directed(&S->in, S->nbr, S->ls_k, tour);
+    else orc_two_opt(&S->in, S->nbr, S->ls_k, tour);
+}
+
 /* Reading: T_NN starts at node 0 (Algorithm 1 does not say where). */
 static void nn_tour(orc_state *S)
 {
@@ -784,7 +882,7 @@ static void nn_tour(orc_state *S)
         S->nn_tour[s] = j;
         S->visited[j] = 1;
     }
-    if (S->p.local_search == 1 || S->p.local_search == 2) orc_two_opt(&S->in, S->nbr, S->ls_k, S->nn_tour);
+    if (S->p.local_search == 1 || S->p.local_search == 2) orc_local_2opt(S, S->nn_tour);
     if (S->p.local_search >= 3) orc_three_opt(&S->in, S->nbr, S->ls_k, S->nn_tour);
     S->L_nn = orc_tour_length(&S->in, S->nn_tour);
 }
@@ -939,7 +1037,7 @@ static void iterate_once(orc_state *S)
     for (int a = 0; a < m; ++a) construct(S, a, S->tours + (int64_t)a * n, &S->lens[a]);
     if (S->p.local_search == 2 || S->p.local_search == 4)   /* Algorithm 1: local search on every ant */
         for (int a = 0; a < m; ++a) {
-            if (S->p.local_search == 2) orc_two_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
+            if (S->p.local_search == 2) orc_local_2opt(S, S->tours + (int64_t)a * n);
             else orc_three_opt(&S->in, S->nbr, S->ls_k, S->tours + (int64_t)a * n);
             S->lens[a] = orc_tour_length(&S->in, S->tours + (int64_t)a * n);
         }
@@ -948,7 +1046,7 @@ static void iterate_once(orc_state *S)
     memcpy(S->ib_tour, S->tours + (int64_t)ib * n, (size_t)n * sizeof(int32_t));
     S->L_ib = S->lens[ib];
     if (S->p.local_search == 1 || S->p.local_search == 3) {   /* local search on T_ib before it is used */
-        if (S->p.local_search == 1) orc_two_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
+        if (S->p.local_search == 1) orc_local_2opt(S, S->ib_tour);
         else orc_three_opt(&S->in, S->nbr, S->ls_k, S->ib_tour);
         S->L_ib = orc_tour_length(&S->in, S->ib_tour);
     }
@@ -1040,10 +1138,11 @@ static int check_inputs(const orc_instance *in, const orc_params *p)
     if (p->schedule != 0 && p->schedule != 1) return ORC_EINVAL;
     if (p->kappa_mode < 0 || p->kappa_mode > 2) return ORC_EINVAL;
     if (p->local_search < 0 || p->local_search > 4) return ORC_EINVAL;
-    if (p->local_search && (in->kind != 0 || p->ls_k < 1 || p->ls_k > in->n - 1)) return ORC_EINVAL;
+    if (p->local_search && (p->ls_k < 1 || p->ls_k > in->n - 1)) return ORC_EINVAL;
+    if (p->local_search >= 3 && in->kind != 0) return ORC_EINVAL;   /* 3-opt: symmetric only */
     /* the 2-opt's FP32 pre-test needs finite squared coordinate differences:
      * |x|, |y| <= 1e18 with local search (the CUDA path checks the same) */
-    if (p->local_search)
+    if (p->local_search && in->kind == 0)
         for (int64_t q = 0; q < 2 * (int64_t)in->n; ++q)
             if (!(fabs((double)in->coords[q]) <= 1e18)) return ORC_EINVAL;
     return ORC_OK;

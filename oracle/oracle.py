@@ -77,6 +77,7 @@ def lib():
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_two_opt.argtypes = [C.POINTER(_Inst), C.c_void_p, C.c_int, C.c_void_p]
         L.orc_three_opt.argtypes = [C.POINTER(_Inst), C.c_void_p, C.c_int, C.c_void_p]
+        L.orc_two_opt_directed.argtypes = [C.POINTER(_Inst), C.c_void_p, C.c_int, C.c_void_p]
         L.orc_tour_length.argtypes = [C.POINTER(_Inst), C.c_void_p]
         L.orc_tour_length.restype = C.c_double
         L.orc_dist.argtypes = [C.POINTER(_Inst), C.c_int, C.c_int]; L.orc_dist.restype = C.c_double
@@ -224,6 +225,14 @@ def two_opt(inst, nbr, tour):
     nb = np.ascontiguousarray(nbr, np.int32)
     t = np.ascontiguousarray(tour, np.int32).copy()
     moves = lib().orc_two_opt(C.byref(h.s), nb.ctypes.data, nb.shape[1], t.ctypes.data)
+    return t, moves
+
+
+def two_opt_directed(inst, nbr, tour):
+    h = _InstHolder(inst)
+    nb = np.ascontiguousarray(nbr, np.int32)
+    t = np.ascontiguousarray(tour, np.int32).copy()
+    moves = lib().orc_two_opt_directed(C.byref(h.s), nb.ctypes.data, nb.shape[1], t.ctypes.data)
     return t, moves
 
 

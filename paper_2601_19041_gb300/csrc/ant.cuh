@@ -149,11 +149,46 @@ struct ClusterList {
     }
 };
 
+// Hillis-Steele inclusive scan (offsets 1, 2, 4) over 8 group totals, of
+// which only the first GT can be non-zero; the exclusive prefix of group g is
+// ex(g) = C[g-1] and the total is C[7].  Additions of a known +0 are skipped
+// (exact for non-negative operands).
+template <int GT>
+struct GroupScan {
+    float C[8];
+    __device__ __forceinline__ void run(const float (&T)[8])
+    {
+        float A[8], B[8];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const bool zg = g >= GT, zp = g - 1 >= GT;   // T[g], T[g-1] known zero
+            if (g == 0 || zp) A[g] = zg ? 0.0f : T[g];
+            else A[g] = zg ? T[g - 1] : __fadd_rn(T[g], T[g - 1]);
+        }
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const bool zg = g - 1 >= GT, zp = g - 3 >= GT;   // A[g], A[g-2] known zero
+            if (g < 2 || zp) B[g] = A[g];
+            else B[g] = zg ? A[g - 2] : __fadd_rn(A[g], A[g - 2]);
+        }
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const bool zg = g - 3 >= GT, zp = g - 7 >= GT;   // B[g], B[g-4] known zero
+            if (g < 4 || zp) C[g] = B[g];
+            else C[g] = zg ? B[g - 4] : __fadd_rn(B[g], B[g - 4]);
+        }
+    }
+};
+
 // Builds the tours of the warp's APW ants (ants a = a_first + seg, real when
 // a < a_end) in iteration t.  vis_warp: APW bitmasks of `stride` words.
+// NGS > 0: every lane gathers the first NGS group totals of its segment (one
+// shuffle each, all independent) and evaluates the Hillis-Steele scan in
+// registers (GroupScan), instead of three dependent shuffle rounds; NGS must
+// be at least k_pad/4 of every instance.  Same values either way.
 // Tours (and the chosen slot of every step, 0xff for a nearest-unvisited
 // step) are written ant-major; lengths are summed afterwards (lengths.cuh).
-template <int APW, typename Rows, typename List>
+template <int APW, typename Rows, typename List, int NGS = 0>
 __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, const List &list, int t,
                                             int a_first, int a_end, unsigned *vis_warp, int stride,
                                             const float2 *xy_scan)
@@ -209,20 +244,34 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
         const float w2 = unv(id.z) ? ch.z : 0.0f;
         const float w3 = unv(id.w) ? ch.w : 0.0f;
         const float p0 = w0, p1 = __fadd_rn(p0, w1), p2 = __fadd_rn(p1, w2), p3 = __fadd_rn(p2, w3);
-        float inc = p3;
+        float ex, total;
+        if constexpr (NGS > 0) {
+            float T[8];
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            const float v = __shfl_up_sync(FULL_MASK, inc, o, 8);
-            if ((lane & 7) >= o) inc = __fadd_rn(inc, v);
+            for (int g = 0; g < 8; ++g) T[g] = g < NGS ? __shfl_sync(FULL_MASK, p3, g, 8) : 0.0f;
+            GroupScan<NGS> sc;
+            sc.run(T);
+            total = sc.C[7];
+            const int gq = lane & 7;
+            ex = 0.0f;   // exclusive prefix C[g-1]; +0 for the first group leaves p_c unchanged
+#pragma unroll
+            for (int g = 1; g < NGS; ++g) ex = gq == g ? sc.C[g - 1] : ex;
+        } else {
+            float inc = p3;
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const float v = __shfl_up_sync(FULL_MASK, inc, o, 8);
+                if ((lane & 7) >= o) inc = __fadd_rn(inc, v);
+            }
+            // exclusive prefix; +0 for the first group leaves p_c unchanged (p_c >= 0)
+            const float exu = __shfl_up_sync(FULL_MASK, inc, 1, 8);
+            ex = (lane & 7) == 0 ? 0.0f : exu;
+            total = __shfl_sync(FULL_MASK, inc, 7, SEG);
         }
-        // exclusive prefix; +0 for the first group leaves p_c unchanged (p_c >= 0)
-        const float exu = __shfl_up_sync(FULL_MASK, inc, 1, 8);
-        const float ex = (lane & 7) == 0 ? 0.0f : exu;
         const float S0 = __fadd_rn(ex, p0);
         const float S1 = __fadd_rn(ex, p1);
         const float S2 = __fadd_rn(ex, p2);
         const float S3 = __fadd_rn(ex, p3);
-        const float total = __shfl_sync(FULL_MASK, inc, 7, SEG);
         const float r = __fmul_rn(unif24(x), total);
 
         int hq = -1;

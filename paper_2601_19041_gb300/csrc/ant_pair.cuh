@@ -33,37 +33,6 @@
 
 namespace hac {
 
-// Hillis-Steele inclusive scan (offsets 1, 2, 4) over 8 group totals, of
-// which only the first GT can be non-zero; the exclusive prefix of group g is
-// ex(g) = C[g-1] and the total is C[7].  Additions of a known +0 are skipped
-// (exact for non-negative operands).
-template <int GT>
-struct PairScan {
-    float C[8];
-    __device__ __forceinline__ void run(const float (&T)[8])
-    {
-        float A[8], B[8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const bool zg = g >= GT, zp = g - 1 >= GT;   // T[g], T[g-1] known zero
-            if (g == 0 || zp) A[g] = zg ? 0.0f : T[g];
-            else A[g] = zg ? T[g - 1] : __fadd_rn(T[g], T[g - 1]);
-        }
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const bool zg = g - 1 >= GT, zp = g - 3 >= GT;   // A[g], A[g-2] known zero
-            if (g < 2 || zp) B[g] = A[g];
-            else B[g] = zg ? A[g - 2] : __fadd_rn(A[g], A[g - 2]);
-        }
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            const bool zg = g - 3 >= GT, zp = g - 7 >= GT;   // B[g], B[g-4] known zero
-            if (g < 4 || zp) C[g] = B[g];
-            else C[g] = zg ? B[g - 4] : __fadd_rn(B[g], B[g - 4]);
-        }
-    }
-};
-
 template <int NGL, typename Rows, typename List>
 __device__ __forceinline__ void build_tours_pair(const DevInst &I, const Rows &rows, const List &list, int t,
                                                  int a_first, int a_end, unsigned *vis_warp, int stride,
@@ -145,7 +114,7 @@ __device__ __forceinline__ void build_tours_pair(const DevInst &I, const Rows &r
         }
 #pragma unroll
         for (int g = 2 * NGL; g < 8; ++g) T[g] = 0.0f;
-        PairScan<GT> sc;
+        GroupScan<GT> sc;
         sc.run(T);
         const float total = sc.C[7];
         const float r = __fmul_rn(unif24(x), total);

@@ -94,9 +94,9 @@ int fold_events(hac_batch *bt)
 
 static int plan_fused(hac_batch *bt, std::vector<int32_t> &order)
 {
-    const int q = bt->ex.ants_per_warp;
-    const int apw = (q == 2 || q == 16 || q == 32) ? q : 4;
-    if (apw != bt->ex.ants_per_warp) return HAC_EUNSUPPORTED;   // the fused kernel has no 1-ant-per-warp form
+    const int apw = bt->ex.ants_per_warp;   // 0: chosen per instance (plan_groups)
+    if (apw != 0 && apw != 2 && apw != 4 && apw != 16 && apw != 32)
+        return HAC_EUNSUPPORTED;            // the fused kernel has no 1-ant-per-warp form
     std::vector<int> members(bt->count);
     for (int b = 0; b < bt->count; ++b) members[b] = b;
     return plan_groups(bt->zs, members, apw, bt->ex.cluster_log2, bt->ex.fallback_list, bt->groups, order);
@@ -155,7 +155,7 @@ static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params 
     // work tables
     std::vector<int2> rowmap, slotmap;
     std::vector<int4> warpmap;
-    const int apw = bt->ex.ants_per_warp;
+    const int apw = bt->ex.ants_per_warp ? bt->ex.ants_per_warp : 4;   // per-step path (also the fallback)
     for (int b = 0; b < count; ++b) {
         const Sizes &z = P.zs[b];
         for (int r = 0; r < z.n; r += ROWS_PER_BLOCK) rowmap.push_back(make_int2(b, r));
@@ -183,6 +183,7 @@ static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params 
             }
         } else {
             bt->ex.fused = 0;   // some instance does not fit the fused kernel: per-iteration path
+            if (bt->ex.ants_per_warp == 0) bt->ex.ants_per_warp = 4;
             bt->groups.clear();
         }
     }
@@ -268,8 +269,8 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     hac_exec ex;
     hac_exec_default(&ex);
     if (exec) ex = *exec;
-    if (ex.ants_per_warp == 0) ex.ants_per_warp = 4;
-    if (ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 16 &&
+    if (ex.ants_per_warp == 0 && !ex.fused) ex.ants_per_warp = 4;   // fused: 0 = per instance
+    if (ex.ants_per_warp != 0 && ex.ants_per_warp != 1 && ex.ants_per_warp != 2 && ex.ants_per_warp != 4 && ex.ants_per_warp != 16 &&
         ex.ants_per_warp != 32)
         return HAC_EINVAL;
     if (ex.warps_per_block == 0) ex.warps_per_block = 4;
@@ -320,7 +321,7 @@ static int enqueue_fused(hac_batch *bt, int iters)
             if (bt->fexec) { cudaGraphExecDestroy(bt->fexec); bt->fexec = nullptr; }
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e1 = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups, bt->ex.ants_per_warp,
+            cudaError_t e1 = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups,
                                            iters, bt->stream);
             cudaError_t e2 = cudaStreamEndCapture(bt->stream, &g);
             if (e1 != cudaSuccess) { g_last_cuda = (int)e1; if (e2 == cudaSuccess) cudaGraphDestroy(g); return HAC_ECUDA; }
@@ -336,7 +337,7 @@ static int enqueue_fused(hac_batch *bt, int iters)
     }
     cudaError_t err = cudaSuccess;
     const int k = timed(bt, 3, [&] {
-        err = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups, bt->ex.ants_per_warp, iters, bt->stream);
+        err = launch_groups(bt->d_inst, bt->d_order, nullptr, bt->groups, iters, bt->stream);
         return (int)bt->groups.size();
     });
     if (err != cudaSuccess) { g_last_cuda = (int)err; return HAC_ECUDA; }
@@ -598,7 +599,7 @@ int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t co
     if (!workspace || ws_bytes < P.total) return HAC_ENOMEM;
     // candidates: every execution layout (none changes a result)
     std::vector<hac_exec> cands;
-    for (int apw : {16, 4, 2, 32})
+    for (int apw : {0, 16, 4, 2, 32})
         for (int clog = 0; clog <= 2; ++clog)
             for (int fbl : {FBL_LEN, 0}) {
                 hac_exec e;

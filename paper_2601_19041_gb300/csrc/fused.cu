@@ -21,7 +21,7 @@
 #include "ant_lane.cuh"
 #include "ant_pair.cuh"
 #include "iter.cuh"
-#include "twoopt.cuh"
+#include "threeopt.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -123,16 +123,21 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
                 if (list_shared) build_tours_pair<NG>(I, rows, clist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
                 else build_tours_pair<NG>(I, rows, glist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
             } else {
-                if (list_shared) build_tours<APW>(I, rows, clist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
-                else build_tours<APW>(I, rows, glist, t, a_first, a_hi, vis_w, A.stride, xy_scan);
+                if (list_shared)
+                    build_tours<APW, ClusterRows<CLOG>, ClusterList<CLOG>, NG>(I, rows, clist, t, a_first, a_hi,
+                                                                             vis_w, A.stride, xy_scan);
+                else
+                    build_tours<APW, ClusterRows<CLOG>, GlobalList, NG>(I, rows, glist, t, a_first, a_hi, vis_w,
+                                                                      A.stride, xy_scan);
             }
         }
         __syncthreads();
         fallback_distances(I, a_lo, a_hi);     // this CTA's ants only: no cluster barrier needed
-        if (I.local_search == 2) {             // Algorithm 1's local search on every ant, each warp its own
-            for (int a = a_first; a < min(a_first + APW, a_hi); ++a) {
+        if (I.local_search == 2 || I.local_search == 4) {   // Algorithm 1's local search on every ant
+            for (int a = a_first; a < min(a_first + APW, a_hi); ++a) {   // each warp its own
                 int32_t *tour = I.tours + (size_t)a * n;
-                warp_two_opt(I, tour, ls_ant(I, a));
+                if (I.local_search == 4) warp_three_opt(I, tour, ls_ant(I, a));
+                else warp_two_opt_any(I, tour, ls_ant(I, a));
                 const double L = warp_tour_length(I, tour);
                 if (lane == 0) I.lens[a] = L;
             }
@@ -144,9 +149,10 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
         cl.sync();
         if (rank == 0) {
             block_iteration_best(I, st);
-            if (I.local_search == 1) {
+            if (I.local_search == 1 || I.local_search == 3) {
                 if (wib == 0) {
-                    warp_two_opt(I, I.ib_tour, ls_global(I, I.ib_tour));
+                    if (I.local_search == 3) warp_three_opt(I, I.ib_tour, ls_global(I, I.ib_tour));
+                    else warp_two_opt_any(I, I.ib_tour, ls_global(I, I.ib_tour));
                     const double L = warp_tour_length(I, I.ib_tour);
                     if (lane == 0) st->L_ib = L;
                 }
@@ -258,8 +264,13 @@ cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, const in
         if (G <= 6) { CLUSTER_SWITCH(16, 3) }
         CLUSTER_SWITCH(16, 4)
     }
-    if (apw == 2) { CLUSTER_SWITCH(2, 0) }
-    CLUSTER_SWITCH(4, 0)
+    // 2 or 4 ants per warp: the group totals are gathered (5 groups for k <= 20, else 8)
+    if (apw == 2) {
+        if (kp_cap <= 20) { CLUSTER_SWITCH(2, 5) }
+        CLUSTER_SWITCH(2, 8)
+    }
+    if (kp_cap <= 20) { CLUSTER_SWITCH(4, 5) }
+    CLUSTER_SWITCH(4, 8)
 #undef CLUSTER_SWITCH
 }
 

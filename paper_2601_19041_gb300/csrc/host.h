@@ -64,7 +64,7 @@ inline int check_params(const hac_instance &in, const hac_params &p)
     if (p.kappa_mode < 0 || p.kappa_mode > 2) return HAC_EINVAL;
     if (p.local_search < 0 || p.local_search > 4) return HAC_EINVAL;
     if (p.local_search) {
-        if (in.kind != 0) return HAC_EUNSUPPORTED;
+        if (in.kind != 0 && p.local_search >= 3) return HAC_EUNSUPPORTED;   // 3-opt: symmetric only
         if (p.ls_k < 1 || p.ls_k > 32 || p.ls_k > in.n - 1) return HAC_EINVAL;
     }
     if (in.symmetrize != 0 && in.symmetrize != 1) return HAC_EINVAL;
@@ -244,7 +244,7 @@ inline int plan_batch(const hac_instance *ins, const hac_params *ps, int count, 
 
 
 struct FusedGroup {
-    int clog = 0, count = 0, order_off = 0;
+    int clog = 0, apw = 4, count = 0, order_off = 0;
     int rows_cap = 0, kp_cap = 0, stride = 0, warps = 0, xy_cap = 0, list_rows = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -319,79 +319,111 @@ inline int upload_inputs(const DevInst &D, const hac_instance &in, const Sizes &
     return HAC_OK;
 }
 
-// Groups the given instances by cluster size (the fewest CTAs whose shared
-// memory holds the instance's share of the candidate table and visited masks,
-// at least 2^clog_min), each group ordered by decreasing work.  `order` lists
+// Groups the given instances by layout: ants per warp and cluster size (the
+// fewest CTAs whose shared memory holds the instance's share of the
+// candidate table and visited masks, at least 2^clog_min), each group ordered
+// by decreasing work.  apw = 0 chooses per instance ("mixed"): 4 ants per warp
+// on one CTA where the instance fits one with its coordinates and lookup
+// lists (many ants per SM), else 2 ants per warp on the smallest cluster that
+// holds it (fewer ants per SM, a shorter step for the large instances that
+// bound the batch).  `order` lists
 // instance indices group after group.
 inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &members, int apw,
                        int clog_min, int fallback_list, std::vector<FusedGroup> &groups,
                        std::vector<int32_t> &order)
 {
     const int count = (int)members.size();
-    std::vector<int> clog(count, -1);
-    auto fits = [&](int q, int cl, int &rows, int &warps) {
+    std::vector<int> clog(count, -1), qapw(count, apw);
+    auto fits = [&](int q, int cl, int a, int &rows, int &warps) {
         const Sizes &z = zs[members[q]];
         const int C = 1 << cl;
         rows = (z.n + C - 1) / C;
         const int apc = (z.m + C - 1) / C;
-        warps = (apc + apw - 1) / apw;
+        warps = (apc + a - 1) / a;
         if (warps > 16) return false;   // k_fused is compiled for at most 512 threads
-        return fused_smem_bytes(rows, z.kp, warps, apw, (z.n + 32) / 32, 0, 0) <= FUSED_SMEM_LIMIT;
+        return fused_smem_bytes(rows, z.kp, warps, a, (z.n + 32) / 32, 0, 0) <= FUSED_SMEM_LIMIT;
     };
     for (int q = 0; q < count; ++q) {
         if (zs[members[q]].n > 65534) return HAC_EUNSUPPORTED;
         int rows, warps;
+        if (apw == 0) {
+            // one CTA only when its coordinates and lookup lists fit beside the table too
+            const Sizes &z = zs[members[q]];
+            if (clog_min == 0 && fits(q, 0, 4, rows, warps) &&
+                fused_smem_bytes(rows, z.kp, warps, 4, (z.n + 32) / 32, z.n, fallback_list ? rows : 0) <=
+                    FUSED_SMEM_LIMIT) {
+                clog[q] = 0;
+                qapw[q] = 4;
+                continue;
+            }
+            qapw[q] = 2;
+        }
         for (int cl = clog_min; cl <= 3; ++cl)
-            if (fits(q, cl, rows, warps)) { clog[q] = cl; break; }
+            if (fits(q, cl, qapw[q], rows, warps)) { clog[q] = cl; break; }
         if (clog[q] < 0) return HAC_EUNSUPPORTED;
     }
+    const int apws[4] = {2, 4, 16, 32};
     for (;;) {   // group caps may exceed the limit when members differ: move a group up
         groups.clear();
         bool again = false;
-        for (int cl = 0; cl <= 3 && !again; ++cl) {
-            FusedGroup G;
-            G.clog = cl;
-            for (int q = 0; q < count; ++q) {
-                if (clog[q] != cl) continue;
-                int rows, warps;
-                fits(q, cl, rows, warps);
-                const Sizes &z = zs[members[q]];
-                G.count++;
-                G.rows_cap = std::max(G.rows_cap, rows);
-                G.kp_cap = std::max(G.kp_cap, z.kp);
-                G.stride = std::max(G.stride, (z.n + 32) / 32);   // bits 0..n (n: padding)
-                G.warps = std::max(G.warps, warps);
+        for (int cl = 0; cl <= 3 && !again; ++cl)
+            for (int ai = 0; ai < 4 && !again; ++ai) {
+                const int a = apws[ai];
+                FusedGroup G;
+                G.clog = cl;
+                G.apw = a;
+                for (int q = 0; q < count; ++q) {
+                    if (clog[q] != cl || qapw[q] != a) continue;
+                    int rows, warps;
+                    fits(q, cl, a, rows, warps);
+                    const Sizes &z = zs[members[q]];
+                    G.count++;
+                    G.rows_cap = std::max(G.rows_cap, rows);
+                    G.kp_cap = std::max(G.kp_cap, z.kp);
+                    G.stride = std::max(G.stride, (z.n + 32) / 32);   // bits 0..n (n: padding)
+                    G.warps = std::max(G.warps, warps);
+                }
+                if (!G.count) continue;
+                const size_t base = fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, a, G.stride, 0, 0);
+                if (base > FUSED_SMEM_LIMIT) {
+                    if (cl == 3) return HAC_EUNSUPPORTED;
+                    for (int q = 0; q < count; ++q) if (clog[q] == cl && qapw[q] == a) clog[q] = cl + 1;
+                    again = true;
+                    break;
+                }
+                // coordinates of the fallback scan in shared memory when they still fit
+                int nmax = 0;
+                for (int q = 0; q < count; ++q)
+                    if (clog[q] == cl && qapw[q] == a) nmax = std::max(nmax, zs[members[q]].n);
+                if (base + (size_t)nmax * 8 <= FUSED_SMEM_LIMIT) G.xy_cap = nmax;
+                // and the lookup lists of this CTA's rows
+                if (fallback_list &&
+                    fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, a, G.stride, G.xy_cap, G.rows_cap) <=
+                        FUSED_SMEM_LIMIT)
+                    G.list_rows = G.rows_cap;
+                groups.push_back(G);
             }
-            if (!G.count) continue;
-            const size_t base = fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, 0, 0);
-            if (base > FUSED_SMEM_LIMIT) {
-                if (cl == 3) return HAC_EUNSUPPORTED;
-                for (int q = 0; q < count; ++q) if (clog[q] == cl) clog[q] = cl + 1;
-                again = true;
-                break;
-            }
-            // coordinates of the fallback scan in shared memory when they still fit
-            int nmax = 0;
-            for (int q = 0; q < count; ++q) if (clog[q] == cl) nmax = std::max(nmax, zs[members[q]].n);
-            if (base + (size_t)nmax * 8 <= FUSED_SMEM_LIMIT) G.xy_cap = nmax;
-            // and the lookup lists of this CTA's rows
-            if (fallback_list &&
-                fused_smem_bytes(G.rows_cap, G.kp_cap, G.warps, apw, G.stride, G.xy_cap, G.rows_cap) <=
-                    FUSED_SMEM_LIMIT)
-                G.list_rows = G.rows_cap;
-            groups.push_back(G);
-        }
         if (!again) break;
     }
+    // groups in order of their largest instance's work: the group launched
+    // first gets SMs first, and the largest instances bound the batch
+    auto work = [&](int i) { const Sizes &z = zs[i]; return (long long)z.m * z.n * z.iters; };
+    std::vector<long long> gmax(groups.size(), 0);
+    for (size_t g = 0; g < groups.size(); ++g)
+        for (int q = 0; q < count; ++q)
+            if (clog[q] == groups[g].clog && qapw[q] == groups[g].apw) gmax[g] = std::max(gmax[g], work(members[q]));
+    std::vector<size_t> gi(groups.size());
+    for (size_t g = 0; g < gi.size(); ++g) gi[g] = g;
+    std::stable_sort(gi.begin(), gi.end(), [&](size_t x, size_t y) { return gmax[x] > gmax[y]; });
+    std::vector<FusedGroup> sorted;
+    for (size_t g : gi) sorted.push_back(groups[g]);
+    groups.swap(sorted);
     order.clear();
     for (FusedGroup &G : groups) {
         G.order_off = (int)order.size();
         std::vector<int32_t> mem;
-        for (int q = 0; q < count; ++q) if (clog[q] == G.clog) mem.push_back(members[q]);
-        std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) {
-            const Sizes &a = zs[x], &c = zs[y];
-            return (long long)a.m * a.n * a.iters > (long long)c.m * c.n * c.iters;
-        });
+        for (int q = 0; q < count; ++q) if (clog[q] == G.clog && qapw[q] == G.apw) mem.push_back(members[q]);
+        std::stable_sort(mem.begin(), mem.end(), [&](int x, int y) { return work(x) > work(y); });
         order.insert(order.end(), mem.begin(), mem.end());
     }
     return HAC_OK;
@@ -401,7 +433,7 @@ inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &mem
 // streams, forked from and joined back into `s`.  d_iters (parallel to
 // d_order, may be null) holds per-instance iteration counts.
 inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
-                                 const std::vector<FusedGroup> &groups, int apw, int iters, cudaStream_t s)
+                                 const std::vector<FusedGroup> &groups, int iters, cudaStream_t s)
 {
     cudaError_t err = cudaSuccess;
     for (size_t g = 1; g < groups.size(); ++g) {
@@ -411,7 +443,7 @@ inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order, 
     for (size_t g = 0; g < groups.size(); ++g) {
         const FusedGroup &G = groups[g];
         cudaError_t e = launch_fused(d_inst, d_order + G.order_off, d_iters ? d_iters + G.order_off : nullptr,
-                                     G.count, G.clog, apw, G.warps,
+                                     G.count, G.clog, G.apw, G.warps,
                                      G.rows_cap, G.kp_cap, G.stride, G.xy_cap, G.list_rows, iters,
                                      g ? G.side : s);
         if (e != cudaSuccess && err == cudaSuccess) err = e;

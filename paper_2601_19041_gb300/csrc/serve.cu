@@ -223,7 +223,7 @@ int enqueue_groups(hac_server *sv, std::vector<FusedGroup> &groups, const int32_
         groups[g].fork = sv->fork[g - 1];
         groups[g].join = sv->join[g - 1];
     }
-    cudaError_t e = launch_groups(sv->d_inst, d_order, d_iters, groups, sv->ex.ants_per_warp, 0, sv->stream);
+    cudaError_t e = launch_groups(sv->d_inst, d_order, d_iters, groups, 0, sv->stream);
     if (e != cudaSuccess) { g_last_cuda = (int)e; return HAC_ECUDA; }
     sv->launches += (long long)groups.size();
     return HAC_OK;

@@ -243,10 +243,166 @@ __device__ __forceinline__ bool ls3_examine(const DevInst &I, const LsMem &M, in
     return false;
 }
 
+// ---------------------------------------------------------------------------
+// Directed 2-opt for the ATSP (Sec. III-D; the reading of the Jonker-Volgenant
+// based 2-opt): the move removes two arcs, adds two arcs and reverses the
+// path between them, so its gain adds the path's forward arc sum F and
+// subtracts its backward sum R.  Examined city a, successor side first:
+//   a+ = succ(a), b over nbr(a) while g1 = c(a,a+) - c(a,b) > 0 (b = a+ or
+//   succ(b) = a skipped): remove (a,a+), (b,b+), add (a,b), (a+,b+),
+//   reverse a+ .. b, gain = (((g1 + c(b,b+)) - c(a+,b+)) + F) - R;
+//   predecessor side: a- = pred(a), g1 = c(a-,a) - c(a,b) (b = a- or
+//   pred(b) = a skipped): remove (a-,a), (b-,b), add (a-,b-), (a,b), reverse
+//   a .. b-, gain = (((g1 + c(b-,b)) - c(a-,b-)) + F) - R.
+// F and R are summed in the order of the tour length (arc k of the path into
+// lane k mod 32, then the pairwise tree), the path always reversed in place.
+
+__device__ __forceinline__ double ls_arc(const DevInst &I, int n, int u, int v)
+{
+    return (double)I.cost[(size_t)u * n + v];
+}
+
+// forward (backward = false) or backward arc sum of the path of len cities
+// starting at position i0 (whole warp, every lane gets the result)
+__device__ __forceinline__ double ls_path_cost(const DevInst &I, const LsMem &M, int n, int i0, int len, bool backward)
+{
+    const int lane = threadIdx.x & 31;
+    double P = 0.0;
+    for (int k = lane; k + 1 < len; k += 32) {
+        int p0 = i0 + k, p1 = i0 + k + 1;
+        if (p0 >= n) p0 -= n;
+        if (p1 >= n) p1 -= n;
+        const int u = M.tour[p0], v = M.tour[p1];
+        P = __dadd_rn(P, backward ? ls_arc(I, n, v, u) : ls_arc(I, n, u, v));
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) P = __dadd_rn(P, __shfl_xor_sync(FULL2, P, o));
+    return P;
+}
+
+// reverses positions i0 .. i0+len-1 (cyclic) in place (whole warp)
+__device__ __forceinline__ void ls_reverse_path(const LsMem &M, int n, int i0, int len)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int t = lane; t < len / 2; t += 32) {
+        int p = i0 + t, q = i0 + len - 1 - t;
+        if (p >= n) p -= n;
+        if (q >= n) q -= n;
+        const int u = M.tour[p], v = M.tour[q];
+        M.tour[p] = v;
+        M.tour[q] = u;
+        M.pos[v] = p;
+        M.pos[u] = q;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool ls2d_examine(const DevInst &I, const LsMem &M, int n, int K, int a)
+{
+    const int lane = threadIdx.x & 31;
+    for (int dir = 0; dir < 2; ++dir) {
+        const int pa = M.pos[a];
+        const int x = dir == 0 ? M.tour[pa + 1 == n ? 0 : pa + 1] : M.tour[pa == 0 ? n - 1 : pa - 1];
+        const double cx = dir == 0 ? ls_arc(I, n, a, x) : ls_arc(I, n, x, a);
+        const int bl = lane < K ? I.nbr[(size_t)a * K + lane] : 0;
+        const double g1l = lane < K ? __dsub_rn(cx, I.nbrd[(size_t)a * K + lane]) : 0.0;
+        const unsigned stop = __ballot_sync(FULL2, lane >= K || !(g1l > 0.0));
+        const int Q = stop ? __ffs(stop) - 1 : 32;
+        for (int q = 0; q < Q; ++q) {
+            const int b = __shfl_sync(FULL2, bl, q);
+            const double g1 = __shfl_sync(FULL2, g1l, q);
+            const int pb = M.pos[b];
+            const int y = dir == 0 ? M.tour[pb + 1 == n ? 0 : pb + 1] : M.tour[pb == 0 ? n - 1 : pb - 1];
+            if (b == x || y == a) continue;
+            const int i0 = dir == 0 ? M.pos[x] : pa;
+            const int i1 = dir == 0 ? pb : M.pos[y];
+            int len = i1 - i0;
+            if (len < 0) len += n;
+            len += 1;
+            const double F = ls_path_cost(I, M, n, i0, len, false);
+            const double R = ls_path_cost(I, M, n, i0, len, true);
+            const double cby = dir == 0 ? ls_arc(I, n, b, y) : ls_arc(I, n, y, b);
+            const double gain = __dsub_rn(__dadd_rn(__dsub_rn(__dadd_rn(g1, cby), ls_arc(I, n, x, y)), F), R);
+            if (gain > LS_GAIN) {
+                ls_reverse_path(M, n, i0, len);
+                if (lane == 0) { M.dlb[a] = 0; M.dlb[x] = 0; M.dlb[b] = 0; M.dlb[y] = 0; }
+                __syncwarp();
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+// passes and rounds of the neighbour-list searches with don't-look bits
+// (as the 2-opt): examine(a) finds and applies one move of city a
+template <typename Examine>
+__device__ __forceinline__ void ls_rounds(const LsMem &M, int n, Examine &&examine)
+{
+    const int lane = threadIdx.x & 31;
+    const long long max_moves = 64LL * n + 1024;
+    long long moves = 0;
+    int round_moves;
+    do {
+        round_moves = 0;
+        for (int p = lane; p < n; p += 32) M.dlb[p] = 0;
+        __syncwarp();
+        bool improved = true;
+        while (improved && moves < max_moves) {
+            improved = false;
+            int p = 0;
+            while (p < n && moves < max_moves) {
+                const int pp = p + lane;
+                const bool clear = pp < n && !M.dlb[M.tour[pp]];
+                const unsigned cm = __ballot_sync(FULL2, clear);
+                if (!cm) { p += 32; continue; }
+                p += __ffs(cm) - 1;
+                const int a = M.tour[p];
+                for (;;) {
+                    if (!examine(a)) break;
+                    improved = true;
+                    ++round_moves;
+                    ++moves;
+                    if (moves >= max_moves) break;
+                }
+                if (lane == 0) M.dlb[a] = 1;
+                __syncwarp();
+                ++p;
+            }
+        }
+    } while (round_moves > 0 && moves < max_moves);
+}
+
+// Improves the ATSP `tour` (global memory) in place by the directed 2-opt.
+static __device__ __noinline__ void warp_two_opt_directed(const DevInst &I, int32_t *tour, const LsMem &Mref)
+{
+    const LsMem M = Mref;   // a local copy: see warp_two_opt
+    const int lane = threadIdx.x & 31;
+    const int n = I.n, K = I.ls_k;
+    if (M.tour != tour)
+        for (int p = lane; p < n; p += 32) M.tour[p] = tour[p];
+    __syncwarp();
+    for (int p = lane; p < n; p += 32) M.pos[M.tour[p]] = p;
+    __syncwarp();
+    ls_rounds(M, n, [&](int a) { return ls2d_examine(I, M, n, K, a); });
+    if (M.tour != tour)
+        for (int p = lane; p < n; p += 32) tour[p] = M.tour[p];
+    __syncwarp();
+}
+
+// the 2-opt of the instance's kind: symmetric (twoopt.cuh) or directed
+static __device__ __forceinline__ void warp_two_opt_any(const DevInst &I, int32_t *tour, const LsMem &M)
+{
+    if (I.kind == 1) warp_two_opt_directed(I, tour, M);
+    else warp_two_opt(I, tour, M);
+}
+
 // Improves `tour` (global memory) in place; M as for warp_two_opt (its el
 // array serves as the scratch of the middle rewrite).
-static __device__ __noinline__ void warp_three_opt(const DevInst &I, int32_t *tour, const LsMem &M)
+static __device__ __noinline__ void warp_three_opt(const DevInst &I, int32_t *tour, const LsMem &Mref)
 {
+    const LsMem M = Mref;   // a local copy: see warp_two_opt
     const int lane = threadIdx.x & 31;
     const int n = I.n, K = I.ls_k;
     if (M.tour != tour)

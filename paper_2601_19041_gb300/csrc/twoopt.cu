@@ -1,6 +1,6 @@
 // Local-search kernels (one warp per tour, its arrays in shared memory when
-// they fit): 2-opt (local_search 1 and 2, twoopt.cuh) or 3-opt (3 and 4,
-// threeopt.cuh).
+// they fit): 2-opt (local_search 1 and 2; twoopt.cuh, or the directed 2-opt of
+// threeopt.cuh for the ATSP) or 3-opt (3 and 4, threeopt.cuh).
 #include "threeopt.cuh"
 
 namespace hac {
@@ -12,7 +12,7 @@ __global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
     if (!I.local_search) return;
     const LsMem M = ls_shared(I, I.nn_tour, ls_sm, smem_bytes, ls_global(I, I.nn_tour));
     if (I.local_search >= 3) warp_three_opt(I, I.nn_tour, M);
-    else warp_two_opt(I, I.nn_tour, M);
+    else warp_two_opt_any(I, I.nn_tour, M);
     const double L = warp_tour_length(I, I.nn_tour);
     if (threadIdx.x == 0) I.st->L_nn = L;
 }
@@ -24,7 +24,7 @@ __global__ void k_two_opt_ib(const DevInst *insts, unsigned smem_bytes)
     if ((I.local_search != 1 && I.local_search != 3) || !I.st->active) return;
     const LsMem M = ls_shared(I, I.ib_tour, ls_sm, smem_bytes, ls_global(I, I.ib_tour));
     if (I.local_search == 3) warp_three_opt(I, I.ib_tour, M);
-    else warp_two_opt(I, I.ib_tour, M);
+    else warp_two_opt_any(I, I.ib_tour, M);
     const double L = warp_tour_length(I, I.ib_tour);
     if (threadIdx.x == 0) I.st->L_ib = L;
 }
@@ -40,7 +40,7 @@ __global__ void k_two_opt_all(const DevInst *insts, int max_m, unsigned smem_byt
     int32_t *tour = I.tours + (size_t)a * I.n;
     const LsMem M = ls_shared(I, tour, ls_sm, smem_bytes, ls_ant(I, a));
     if (I.local_search == 4) warp_three_opt(I, tour, M);
-    else warp_two_opt(I, tour, M);
+    else warp_two_opt_any(I, tour, M);
     const double L = warp_tour_length(I, tour);
     if (threadIdx.x == 0) I.lens[a] = L;
 }

@@ -285,9 +285,13 @@ __device__ __forceinline__ bool ls_find_move(const DevInst &I, const LsMem &M, i
 }
 
 // Improves `tour` (global memory) in place.  M holds the working arrays; when
-// M.tour is not `tour`, the tour is copied in and back out.
-static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour, const LsMem &M)
+// M.tour is not `tour`, the tour is copied in and back out.  The array
+// pointers are copied into a local first: the search stores through generic
+// pointers, and pointers read through a reference would be reloaded after
+// every store.
+static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour, const LsMem &Mref)
 {
+    const LsMem M = Mref;
     const int lane = threadIdx.x & 31;
     const int n = I.n, K = I.ls_k;
     if (M.tour != tour)
@@ -393,7 +397,7 @@ __device__ __forceinline__ LsMem ls_shared(const DevInst &I, int32_t *tour, unsi
     M.el = reinterpret_cast<float *>(sm + (size_t)n * 8);
     M.dlb = sm + (size_t)n * 12;
     M.xy = reinterpret_cast<const float2 *>(I.xy);
-    if (ls_smem_full(n) <= smem_bytes) {
+    if (I.kind == 0 && ls_smem_full(n) <= smem_bytes) {
         float2 *sxy = reinterpret_cast<float2 *>(sm + ls_xy_offset(n));
         for (int p = threadIdx.x & 31; p < n; p += 32) sxy[p] = reinterpret_cast<const float2 *>(I.xy)[p];
         __syncwarp();

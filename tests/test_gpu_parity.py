@@ -118,6 +118,9 @@ CASES = {
     "three_opt_grid": lambda: (euclid(np.stack(np.meshgrid(np.arange(13), np.arange(13)), -1).reshape(-1, 2) / 12.0),
                                params(m=8, k=10, iterations=5, rho=0.2, local_search=3, ls_k=9, seed=29)),
     "three_opt_every_ant": lambda: (synth.euclid_instance(34, 140, K=10), params(m=7, k=10, iterations=4, rho=0.2, local_search=4, ls_k=12, seed=30)),
+    # the directed 2-opt of the ATSP (Sec. III-D): on T_ib and T_NN; on every ant
+    "atsp_two_opt": lambda: (synth.atsp_instance(35, 180, K=20), params(m=8, k=12, iterations=5, rho=0.2, degree_target=1, local_search=1, ls_k=10, seed=31)),
+    "atsp_two_opt_every_ant": lambda: (synth.atsp_instance(36, 90, K=15), params(m=6, k=10, iterations=4, rho=0.2, degree_target=1, local_search=2, ls_k=8, seed=32)),
     "clustered": lambda: (synth.euclid_instance(25, 300, K=50, family="gmm"), params(m=12, k=20, iterations=6, rho=0.2, seed=19)),
     "grid": lambda: (synth.euclid_instance(26, 289, K=50, family="grid"), params(m=12, k=20, iterations=6, rho=0.2, seed=20)),
 }
@@ -145,7 +148,8 @@ FUSED = [dict(apw=2, clog=0, fbl=32), dict(apw=4, clog=1, fbl=0), dict(apw=4, cl
 @pytest.mark.parametrize("cfg", FUSED, ids=lambda c: f"apw{c['apw']}_C{1 << c['clog']}_fbl{c['fbl']}")
 @pytest.mark.parametrize("name", ["sym50nn_k20", "sym10nn_k10_ragged", "k32", "k7_pad", "n3",
                                   "empty_heatmap", "atsp", "two_opt", "two_opt_grid", "alpha_beta_powers",
-                                  "kappa_no_cap", "three_opt", "three_opt_every_ant"])
+                                  "kappa_no_cap", "three_opt", "three_opt_every_ant", "atsp_two_opt",
+                                  "atsp_two_opt_every_ant"])
 def test_fused_kernel_parity(hac, orc, name, cfg):
     inst, p = CASES[name]()
     if cfg["apw"] == 32 and p.local_search in (2, 4):
@@ -165,6 +169,8 @@ def test_fused_mixed_batch_groups(hac, orc):
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(16, 0, 1, fused=1, fallback_list=32))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(32, 4, 1, fused=0, fallback_list=32))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(16, 4, 1, fused=0, fallback_list=32))
+    # ants per warp chosen per instance: 4 on one CTA where it fits, else 2 on a cluster
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(0, 0, 1, fused=1, fallback_list=32))
 
 
 def test_mixed_batch_parity(hac, orc):
@@ -205,7 +211,11 @@ def test_batch_membership_does_not_change_results(hac):
 def test_full_size_tsp500(hac, orc):
     insts, ps = synth.workload("tsp500")
     run_case(hac, orc, insts, ps)
-    run_case(hac, orc, insts, ps, exec_=hac.make_exec(**BENCH_EXEC))
+    run_case(hac, orc, insts, ps, exec_=_layout(hac, insts, ps, "autotuned"))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(**FIXED_EXEC["apw4"]))
+
+
+_ORACLE_RUNS = {}
 
 
 def _oracle_many(orc, insts, ps):
@@ -216,30 +226,45 @@ def _oracle_many(orc, insts, ps):
         return list(ex.map(one, range(len(insts))))
 
 
-BENCH_EXEC = dict(ants_per_warp=4, fused=1, fallback_list=32)   # what bench.py times by default
+# fixed layouts run at full size besides the autotuner's pick (which is what
+# bench.py times): 4 ants per warp on the fewest CTAs, and 2 ants per warp on
+# clusters of at least 2 CTAs
+FIXED_EXEC = {"apw4": dict(ants_per_warp=4, fused=1, fallback_list=32),
+              "apw2_C2": dict(ants_per_warp=2, fused=1, fallback_list=32, cluster_log2=1)}
 
 
+def _layout(hac, insts, ps, which):
+    if which == "autotuned":                       # the layout bench.py picks and times
+        ex, _ = hac.autotune(insts, ps, trial_iters=10, inputs_on_device=False)
+        return ex
+    return hac.make_exec(**FIXED_EXEC[which])
+
+
+@pytest.mark.parametrize("layout", ["autotuned", "apw4", "apw2_C2"])
 @pytest.mark.parametrize("name,sample", [("batch128", (0, 37, 90, 127)), ("atsp1000", (0, 31, 63))])
-def test_full_size_workload_sampled(hac, orc, name, sample):
+def test_full_size_workload_sampled(hac, orc, name, sample, layout):
     insts, ps = synth.workload(name)
-    bt = hac.Batch(insts, ps, hac.make_exec(**BENCH_EXEC))
+    bt = hac.Batch(insts, ps, _layout(hac, insts, ps, layout))
     try:
         bt.run().sync()
-        sub_i = [insts[b] for b in sample]
-        sub_p = [ps[b] for b in sample]
-        oracles = _oracle_many(orc, sub_i, sub_p)
-        for b, o in zip(sample, oracles):
+        key = (name, sample)
+        if key not in _ORACLE_RUNS:                # the same for every layout
+            _ORACLE_RUNS[key] = _oracle_many(orc, [insts[b] for b in sample], [ps[b] for b in sample])
+        for b, o in zip(sample, _ORACLE_RUNS[key]):
             search_equal(bt, b, o, ps[b].iterations)
     finally:
         bt.close()
 
 
-def test_full_size_tsp10k_two_opt_sampled(hac, orc):
+@pytest.mark.parametrize("layout", ["autotuned", "apw4"])
+def test_full_size_tsp10k_two_opt_sampled(hac, orc, layout):
     insts, ps = synth.workload("tsp10k_2opt")
-    bt = hac.Batch(insts, ps, hac.make_exec(**BENCH_EXEC))
+    bt = hac.Batch(insts, ps, _layout(hac, insts, ps, layout))
     try:
         bt.run().sync()
-        o = _oracle_many(orc, [insts[5]], [ps[5]])[0]
+        if "tsp10k" not in _ORACLE_RUNS:
+            _ORACLE_RUNS["tsp10k"] = _oracle_many(orc, [insts[5]], [ps[5]])[0]
+        o = _ORACLE_RUNS["tsp10k"]
         search_equal(bt, 5, o, ps[5].iterations)
         D_ok = is_perm(bt.read(5, "GB_TOUR"), 10000)
         assert D_ok

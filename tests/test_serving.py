@@ -170,3 +170,28 @@ def test_upload_ring_wraps_without_corrupting_inputs(hac):
         ref_t, ref_l = hac.solve(i, p)
         assert np.array_equal(out[t][0], ref_t)
         assert out[t][1] == ref_l
+
+
+def test_full_size_request_on_the_per_step_route(hac, orc):
+    """A stream-sized request (n = 5000, FP16 heatmap) goes to the per-step
+    kernels (step_min_n = 3000, as the serving benchmark runs them) while a
+    small one runs in the cluster kernel; both equal the oracle (few
+    iterations keep the oracle cheap)."""
+    big = synth.euclid_instance(40123, 5000, K=50, family="gmm", dtype=np.float16)
+    pbig = synth.Params(m=64, k=20, iterations=3, rho=0.2, seed=40123)
+    small = synth.euclid_instance(40124, 500, K=50, family="grid", dtype=np.float16)
+    psmall = synth.Params(m=64, k=20, iterations=5, rho=0.2, seed=40124)
+    srv = hac.Server(1 << 30, max_slots=8, iters_per_tick=10, max_n=10000, steps_per_tick=4000, step_min_n=3000,
+                     step_ants_per_warp=1, step_warps_per_block=8,
+                     exec_=hac.make_exec(ants_per_warp=4, fused=1, fallback_list=32))
+    try:
+        tb = srv.submit(big, pbig)
+        ts = srv.submit(small, psmall)
+        out = {}
+        _drain(srv, [tb, ts], out)
+    finally:
+        srv.close()
+    for t, (inst, p) in ((tb, (big, pbig)), (ts, (small, psmall))):
+        o = orc.Oracle(inst, p).iterate(p.iterations)
+        assert np.array_equal(out[t][0], o.get("gb_tour"))
+        assert out[t][1] == o.scalars()["L_gb"]
