@@ -77,9 +77,13 @@ def parse():
     ap.add_argument("--fused", type=int, default=1, help="1: persistent fused cluster kernel")
     ap.add_argument("--fbl", type=int, default=32, help="nearest-unvisited lookup list (0 or 32)")
     ap.add_argument("--clog", type=int, default=0, help="fused: at least 2^clog CTAs per instance")
+    ap.add_argument("--parts", type=int, default=0, help="per-step kernels: instance parts on own streams")
     ap.add_argument("--plain-sample", type=int, default=4,
                     help="instances decoded one per launch sequence for the plain-GPU comparison (0: skip)")
     ap.add_argument("--iters", type=int, default=0, help="override the iteration count (profiling)")
+    ap.add_argument("--uniform-n", type=int, default=0,
+                    help="profiling: replace the workload's instances by --count uniform instances of this n "
+                         "(50-NN heatmaps, m=64, k=20, rho=0.2, seeds 1000+b)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: pick the execution layout with hac_batch_autotune before the warm-up (untimed); "
                          "0: use --apw/--wpb/--fused/--fbl/--clog as given")
@@ -104,8 +108,11 @@ def dist_env():
 # DRAM bytes per fused launch measured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) for a workload and layout; the summary with its
 # command is in profiles/dram_traffic_batch128_n500-2000.md.  Reported as
-# roofline.traffic only for the same workload and layout.
-NCU_TRAFFIC = {("batch128", 1, 2, 32, 0, 200): 5.372e9 + 6.298e9}
+# roofline.traffic only for the same workload and layout (2 ants per warp
+# puts every instance of this workload on clusters of 2 CTAs, so a smallest
+# cluster of 1 or 2 is the same launch).
+_T_APW2 = 5.542512128e9 + 6.347278080e9
+NCU_TRAFFIC = {("batch128", 1, 2, 32, 0, 200): _T_APW2, ("batch128", 1, 2, 32, 1, 200): _T_APW2}
 
 
 def load_peaks():
@@ -350,6 +357,10 @@ def run_ours(args):
     build.build()
     L = heataco._lib()
     insts, ps = workload(args.workload, rank, count=args.count or None)
+    if args.uniform_n:
+        cnt = args.count or 16
+        insts = [synth.euclid_instance(1000 + b, args.uniform_n, K=50) for b in range(cnt)]
+        ps = [synth.Params(m=64, k=20, iterations=200, rho=0.2, seed=1000 + b) for b in range(cnt)]
     if args.iters:
         for p in ps:
             p.iterations = args.iters
@@ -373,10 +384,11 @@ def run_ours(args):
         tune = {"seconds": time.perf_counter() - t0, "trial_iters": args.tune_iters,
                 "ms_per_iter": ms_it.value}
         args.apw, args.wpb, args.fused = best.ants_per_warp, best.warps_per_block, best.fused
-        args.fbl, args.clog = best.fallback_list, best.cluster_log2
+        args.fbl, args.clog, args.parts = best.fallback_list, best.cluster_log2, best.parts
     ex = heataco.make_exec(args.apw, args.wpb, use_graph=0, profile=1, fused=args.fused,
-                           fallback_list=args.fbl, cluster_log2=args.clog)
+                           fallback_list=args.fbl, cluster_log2=args.clog, parts=args.parts)
     kgroup = 3 if args.fused else 0
+    region = args.fused or args.parts > 1    # one timed region per step (all iterations)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
     def one_step():
@@ -434,7 +446,7 @@ def run_ours(args):
     # Fused: one launch runs every iteration (construction + update) of a group;
     # its algorithmic bytes are the construction bytes of all iterations.
     hbm_peak, peak_kind = load_peaks()
-    if args.fused:   # one region per step: the concurrent group launches of all iterations
+    if region:       # one region per step: the concurrent group launches of all iterations
         avg_ms = stats["construct_ms"] / args.steps
         per_launch_bytes = alg_bytes * ps[0].iterations
     else:            # one construction launch per iteration
@@ -442,7 +454,9 @@ def run_ours(args):
         per_launch_bytes = alg_bytes
     achieved = per_launch_bytes / (avg_ms / 1000.0) / 1e9
     construct_share = stats["construct_ms"] / dev_ms if dev_ms else None
-    kernel_name = "k_fused (construct + update, all iterations)" if args.fused else "k_construct"
+    kernel_name = ("k_fused (construct + update, all iterations)" if args.fused else
+                   "per-step kernels of all iterations, instance parts on their own streams" if region else
+                   "k_construct")
 
     # latency model: a batch cannot finish before its longest instance, whose
     # iterations are n sequential construction steps each.  Decode that
@@ -517,7 +531,7 @@ def run_ours(args):
         tptr = (C.c_void_p * count)(*[t.data_ptr() for t in tours])
         lens = torch.empty(count, dtype=torch.float64, pin_memory=True)
         ex2 = heataco.make_exec(args.apw, args.wpb, use_graph=1, fused=args.fused,
-                                fallback_list=args.fbl, cluster_log2=args.clog)
+                                fallback_list=args.fbl, cluster_log2=args.clog, parts=args.parts)
         stat = (C.c_int32 * count)()
 
         def e2e_step():
@@ -559,7 +573,8 @@ def run_ours(args):
                        "inputs": "resident in HBM before the timed region",
                        "ants_per_warp": (ex.ants_per_warp or ("per instance: 4 on one CTA, else 2 on a cluster"
                                                                if args.fused else 4)), "fused": args.fused,
-                       "warps_per_block": args.wpb, "cluster_log2": args.clog,
+                       "warps_per_block": args.wpb, "cluster_log2": args.clog, "parts": args.parts,
+                       "uniform_n": args.uniform_n or None,
                        "fallback_list": args.fbl, "autotune": tune,
                        "kernel_timing": "CUDA events per launch"},
             "instances_per_s": inst_per_s,
@@ -694,8 +709,8 @@ def run_serve(args):
     if args.plain_sample:
         P = min(len(reqs), max(1, args.plain_requests))
         exp = heataco.make_exec(2, 8, use_graph=1, fused=0, fallback_list=0)
-        warm = reqs[0]
-        heataco.solve_batch([warm.inst], [synth.Params(**{**warm.params.__dict__, "iterations": 2})], exp)
+        r0 = reqs[0]
+        heataco.solve_batch([r0.inst], [synth.Params(**{**r0.params.__dict__, "iterations": 2})], exp)
         torch.cuda.synchronize()
         t0p = time.perf_counter()
         plat, srv_lat = [], []

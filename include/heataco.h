@@ -144,6 +144,10 @@ typedef struct {
     int32_t fallback_list;    /* 32: look up the 32 nearest nodes (key order) before scanning; 0: scan only */
     int32_t profile;          /* 1: bracket every kernel group with CUDA events (no graphs) */
     int32_t cluster_log2;     /* fused kernel: at least 2^cluster_log2 CTAs per instance (0 = fewest that fit) */
+    int32_t parts;            /* per-step kernels: the instances are split into this many contiguous
+                                 parts of about equal work, each iterated on a stream of its own, so
+                                 one part's local search overlaps another part's construction
+                                 (0 or 1: one part on the batch's stream; at most 64) */
 } hac_exec;
 
 int hac_params_default(hac_params *p, int32_t kind);

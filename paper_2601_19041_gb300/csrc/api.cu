@@ -21,6 +21,19 @@ thread_local int g_last_cuda = 0;
 }
 }  // namespace hac
 
+// a contiguous range of instances iterated on its own stream (per-step path)
+struct BatchPart {
+    int b0 = 0, count = 0;                 // instances b0 .. b0+count-1
+    int warp_off = 0, warp_len = 0;        // slice of the warp table (instance index relative to b0)
+    int slot_off = 0, slot_len = 0;        // slice of the relative slot table
+    int max_n = 0, max_kp = 0, ls_all_m = 0;
+    bool any_ls = false;
+    cudaStream_t stream = nullptr;         // the batch's stream when there is one part
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_kernels = 0;
+};
+
 struct hac_batch {
     int count = 0;
     cudaStream_t stream = nullptr;
@@ -32,6 +45,8 @@ struct hac_batch {
     int rowmap_len = 0;
     int2 *d_slotmap = nullptr;
     int slotmap_len = 0;
+    int2 *d_slotmap_rel = nullptr;      // slot table with instance indices relative to the part
+    std::vector<BatchPart> parts;
     int4 *d_warpmap = nullptr;
     int warpmap_len = 0;
     int32_t *d_order = nullptr;
@@ -41,8 +56,6 @@ struct hac_batch {
     bool any_ls = false;
     int ls_all_m = 0;               // largest m among the instances with local search on every ant
     std::vector<int> t_host;
-    cudaGraphExec_t gexec = nullptr;
-    int graph_kernels = 0;          // kernels inside one graph replay
     cudaGraphExec_t fexec = nullptr;   // fused groups (fork/join included) for fexec_iters iterations
     int fexec_iters = -1;
     long long launches = 0;         // kernels issued so far
@@ -125,6 +138,7 @@ static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params 
     map_sizes(P.zs, rows, slots, warps);
     bt->d_rowmap = (int2 *)(B + A.take(rows * sizeof(int2)));
     bt->d_slotmap = (int2 *)(B + A.take(slots * sizeof(int2)));
+    bt->d_slotmap_rel = (int2 *)(B + A.take(slots * sizeof(int2)));
     bt->d_warpmap = (int4 *)(B + A.take(warps * sizeof(int4)));
     bt->d_order = (int32_t *)(B + A.take((size_t)count * sizeof(int32_t)));
     size_t z0 = A.take(sizeof(int));
@@ -152,20 +166,62 @@ static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params 
         bt->any_ls |= z.ls != 0;
         if (z.ls == 2 || z.ls == 4) bt->ls_all_m = std::max(bt->ls_all_m, z.m);
     }
-    // work tables
-    std::vector<int2> rowmap, slotmap;
+    // parts of the per-step path: contiguous instance ranges of about equal work
+    const int nparts = std::max(1, std::min(std::min((int)bt->ex.parts, 64), count));
+    {
+        long long total = 0;
+        for (int b = 0; b < count; ++b) total += (long long)P.zs[b].m * P.zs[b].n * P.zs[b].iters;
+        long long acc = 0;
+        int b0 = 0;
+        for (int b = 0; b < count; ++b) {
+            acc += (long long)P.zs[b].m * P.zs[b].n * P.zs[b].iters;
+            const int made = (int)bt->parts.size();
+            const bool last = b == count - 1;
+            const bool cut = made + 1 < nparts && acc * nparts >= total * (made + 1) && count - b - 1 >= nparts - made - 1;
+            if (cut || last) {
+                BatchPart pt;
+                pt.b0 = b0;
+                pt.count = b + 1 - b0;
+                bt->parts.push_back(pt);
+                b0 = b + 1;
+            }
+        }
+    }
+    // work tables (warp and relative slot tables part by part)
+    std::vector<int2> rowmap, slotmap, slotrel;
     std::vector<int4> warpmap;
     const int apw = bt->ex.ants_per_warp ? bt->ex.ants_per_warp : 4;   // per-step path (also the fallback)
-    for (int b = 0; b < count; ++b) {
-        const Sizes &z = P.zs[b];
-        for (int r = 0; r < z.n; r += ROWS_PER_BLOCK) rowmap.push_back(make_int2(b, r));
-        const size_t S = (size_t)z.n * z.kp;
-        for (size_t q = 0; q < S; q += SLOTS_PER_BLOCK) slotmap.push_back(make_int2(b, (int)q));
-        for (int a = 0; a < z.m; a += apw) warpmap.push_back(make_int4(b, a, 0, 0));
+    for (BatchPart &pt : bt->parts) {
+        pt.warp_off = (int)warpmap.size();
+        pt.slot_off = (int)slotrel.size();
+        for (int b = pt.b0; b < pt.b0 + pt.count; ++b) {
+            const Sizes &z = P.zs[b];
+            for (int r = 0; r < z.n; r += ROWS_PER_BLOCK) rowmap.push_back(make_int2(b, r));
+            const size_t S = (size_t)z.n * z.kp;
+            for (size_t q = 0; q < S; q += SLOTS_PER_BLOCK) {
+                slotmap.push_back(make_int2(b, (int)q));
+                slotrel.push_back(make_int2(b - pt.b0, (int)q));
+            }
+            for (int a = 0; a < z.m; a += apw) warpmap.push_back(make_int4(b - pt.b0, a, 0, 0));
+            pt.max_n = std::max(pt.max_n, z.n);
+            pt.max_kp = std::max(pt.max_kp, z.kp);
+            pt.any_ls |= z.ls != 0;
+            if (z.ls == 2 || z.ls == 4) pt.ls_all_m = std::max(pt.ls_all_m, z.m);
+        }
+        pt.warp_len = (int)warpmap.size() - pt.warp_off;
+        pt.slot_len = (int)slotrel.size() - pt.slot_off;
+        if (bt->parts.size() == 1) {
+            pt.stream = s;
+        } else {
+            CK(cudaStreamCreateWithFlags(&pt.stream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&pt.fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&pt.join, cudaEventDisableTiming));
+        }
     }
     bt->rowmap_len = (int)rowmap.size();
     bt->slotmap_len = (int)slotmap.size();
     bt->warpmap_len = (int)warpmap.size();
+    CK(cudaMemcpyAsync(bt->d_slotmap_rel, slotrel.data(), slotrel.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(bt->d_rowmap, rowmap.data(), rowmap.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(bt->d_slotmap, slotmap.data(), slotmap.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(bt->d_warpmap, warpmap.data(), warpmap.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
@@ -239,6 +295,7 @@ int hac_exec_default(hac_exec *e)
     e->fallback_list = 0;
     e->profile = 0;
     e->cluster_log2 = 0;
+    e->parts = 0;
     return HAC_OK;
 }
 
@@ -277,6 +334,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     if (ex.warps_per_block < 1 || ex.warps_per_block > 8) return HAC_EINVAL;
     if (ex.fallback_list != 0 && ex.fallback_list != FBL_LEN) return HAC_EINVAL;
     if (ex.cluster_log2 < 0 || ex.cluster_log2 > 3) return HAC_EINVAL;
+    if (ex.parts < 0 || ex.parts > 64) return HAC_EINVAL;
     if (ex.ants_per_warp == 32)   // step-major tours: 2-opt on every ant needs them ant by ant
         for (int b = 0; b < count; ++b)
             if (ps[b].local_search == 2 || ps[b].local_search == 4) return HAC_EUNSUPPORTED;
@@ -299,17 +357,53 @@ static int remaining(const hac_batch *bt)
     return rem;
 }
 
-static int enqueue_iteration(hac_batch *bt)
+static int enqueue_iteration(hac_batch *bt, const BatchPart &pt)
 {
+    const DevInst *d = bt->d_inst + pt.b0;
+    if (bt->parts.size() > 1)   // several parts: no per-group timing (the fork/join region is timed)
+        return launch_construct(d, bt->d_warpmap + pt.warp_off, pt.warp_len, bt->ex.ants_per_warp,
+                                bt->ex.warps_per_block, pt.max_n, pt.max_kp, pt.count, pt.stream) +
+               launch_iteration_tail(d, pt.count, bt->d_slotmap_rel + pt.slot_off, pt.slot_len, pt.any_ls,
+                                     pt.max_n, pt.ls_all_m, pt.stream);
     int k = timed(bt, 0, [&] {
-        return launch_construct(bt->d_inst, bt->d_warpmap, bt->warpmap_len, bt->ex.ants_per_warp,
-                                bt->ex.warps_per_block, bt->max_n, bt->max_kp, bt->count, bt->stream);
+        return launch_construct(d, bt->d_warpmap + pt.warp_off, pt.warp_len, bt->ex.ants_per_warp,
+                                bt->ex.warps_per_block, pt.max_n, pt.max_kp, pt.count, pt.stream);
     });
     k += timed(bt, 1, [&] {
-        return launch_iteration_tail(bt->d_inst, bt->count, bt->d_slotmap, bt->slotmap_len,
-                                     bt->any_ls, bt->max_n, bt->ls_all_m, bt->stream);
+        return launch_iteration_tail(d, pt.count, bt->d_slotmap_rel + pt.slot_off, pt.slot_len, pt.any_ls,
+                                     pt.max_n, pt.ls_all_m, pt.stream);
     });
     return k;
+}
+
+// `todo` iterations of one part on its stream (CUDA graphs of GRAPH_CHUNK
+// iterations when enabled)
+static int iterate_part(hac_batch *bt, BatchPart &pt, int todo)
+{
+    cudaStream_t s = pt.stream;
+    if (bt->ex.use_graph && !bt->ex.profile && s != nullptr && todo >= GRAPH_CHUNK) {
+        if (!pt.gexec) {
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            pt.graph_kernels = 0;
+            for (int q = 0; q < GRAPH_CHUNK; ++q) pt.graph_kernels += enqueue_iteration(bt, pt);
+            cudaError_t e1 = cudaGetLastError();
+            cudaError_t e2 = cudaStreamEndCapture(s, &g);
+            if (e1 != cudaSuccess) { g_last_cuda = (int)e1; if (e2 == cudaSuccess) cudaGraphDestroy(g); return HAC_ECUDA; }
+            CK(e2);
+            cudaError_t e3 = cudaGraphInstantiate(&pt.gexec, g, 0);
+            cudaGraphDestroy(g);
+            CK(e3);
+        }
+        while (todo >= GRAPH_CHUNK) {
+            CK(cudaGraphLaunch(pt.gexec, s));
+            bt->launches += pt.graph_kernels;
+            todo -= GRAPH_CHUNK;
+        }
+    }
+    for (; todo > 0; --todo) bt->launches += enqueue_iteration(bt, pt);
+    CK(cudaGetLastError());
+    return HAC_OK;
 }
 
 // the fused groups run concurrently (launch_groups); with CUDA graphs on, the
@@ -360,27 +454,35 @@ int hac_batch_iterate(hac_batch *bt, int32_t iters)
         for (int b = 0; b < bt->count; ++b) bt->t_host[b] = std::min(bt->zs[b].iters, bt->t_host[b] + done);
         return HAC_OK;
     }
-    if (bt->ex.use_graph && !bt->ex.profile && s != nullptr && todo >= GRAPH_CHUNK) {
-        if (!bt->gexec) {
-            cudaGraph_t g;
-            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            bt->graph_kernels = 0;
-            for (int q = 0; q < GRAPH_CHUNK; ++q) bt->graph_kernels += enqueue_iteration(bt);
-            cudaError_t e1 = cudaGetLastError();
-            cudaError_t e2 = cudaStreamEndCapture(s, &g);
-            if (e1 != cudaSuccess) { g_last_cuda = (int)e1; return HAC_ECUDA; }
-            CK(e2);
-            cudaError_t e3 = cudaGraphInstantiate(&bt->gexec, g, 0);
-            cudaGraphDestroy(g);
-            CK(e3);
-        }
-        while (todo >= GRAPH_CHUNK) {
-            CK(cudaGraphLaunch(bt->gexec, s));
-            bt->launches += bt->graph_kernels;
-            todo -= GRAPH_CHUNK;
+    if (todo > 0) {
+        if (bt->parts.size() == 1) {
+            int st = iterate_part(bt, bt->parts[0], todo);
+            if (st) return st;
+        } else {
+            // the parts run on their own streams, forked from and joined into the batch's
+            int st = HAC_OK;
+            timed(bt, 0, [&] {
+                for (BatchPart &pt : bt->parts) {
+                    cudaEventRecord(pt.fork, s);
+                    cudaStreamWaitEvent(pt.stream, pt.fork, 0);
+                }
+                // chunk by chunk, round robin over the parts, so that no part's
+                // launches fill the launch queue before the next part's start
+                for (int left = todo; left > 0 && !st;) {
+                    const int chunk = std::min(left, GRAPH_CHUNK);
+                    for (BatchPart &pt : bt->parts)
+                        if (!st) st = iterate_part(bt, pt, chunk);
+                    left -= chunk;
+                }
+                for (BatchPart &pt : bt->parts) {
+                    cudaEventRecord(pt.join, pt.stream);
+                    cudaStreamWaitEvent(s, pt.join, 0);
+                }
+                return 0;
+            });
+            if (st) return st;
         }
     }
-    for (; todo > 0; --todo) bt->launches += enqueue_iteration(bt);
     CK(cudaGetLastError());
     for (int b = 0; b < bt->count; ++b) bt->t_host[b] = std::min(bt->zs[b].iters, bt->t_host[b] + done);
     return HAC_OK;
@@ -519,8 +621,13 @@ int hac_batch_kernel_time(hac_batch *bt, int32_t group, double *ms, int64_t *lau
 int hac_batch_destroy(hac_batch *bt)
 {
     if (!bt) return HAC_EINVAL;
-    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
     if (bt->fexec) cudaGraphExecDestroy(bt->fexec);
+    for (BatchPart &pt : bt->parts) {
+        if (pt.gexec) cudaGraphExecDestroy(pt.gexec);
+        if (pt.fork) cudaEventDestroy(pt.fork);
+        if (pt.join) cudaEventDestroy(pt.join);
+        if (pt.stream && pt.stream != bt->stream) cudaStreamDestroy(pt.stream);
+    }
     for (cudaEvent_t e : bt->ev_pool) cudaEventDestroy(e);
     for (FusedGroup &G : bt->groups) {
         if (G.side) cudaStreamDestroy(G.side);
@@ -608,12 +715,15 @@ int hac_batch_autotune(const hac_instance *ins, const hac_params *ps, int32_t co
                 cands.push_back(e);
             }
     for (int apw : {16, 4, 2, 1})
-        for (int wpb : {4, 8}) {
-            hac_exec e;
-            hac_exec_default(&e);
-            e.fused = 0; e.ants_per_warp = apw; e.warps_per_block = wpb; e.fallback_list = FBL_LEN;
-            cands.push_back(e);
-        }
+        for (int wpb : {4, 8})
+            for (int parts : {1, 4}) {
+                if (parts > count) continue;
+                hac_exec e;
+                hac_exec_default(&e);
+                e.fused = 0; e.ants_per_warp = apw; e.warps_per_block = wpb; e.fallback_list = FBL_LEN;
+                e.parts = parts;
+                cands.push_back(e);
+            }
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t ev[2];
     CK(cudaEventCreate(&ev[0]));

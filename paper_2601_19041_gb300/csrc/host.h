@@ -232,6 +232,7 @@ inline int plan_batch(const hac_instance *ins, const hac_params *ps, int count, 
     map_sizes(P.zs, rows, slots, warps);
     A.take(rows * sizeof(int2));
     A.take(slots * sizeof(int2));
+    A.take(slots * sizeof(int2));              // slot table relative to each part's first instance
     A.take(warps * sizeof(int4));
     A.take((size_t)count * sizeof(int32_t));   // fused-kernel cluster -> instance order
     size_t z0 = A.take(sizeof(int));       // error word starts the zero region

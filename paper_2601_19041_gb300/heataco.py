@@ -53,7 +53,7 @@ class hac_params(C.Structure):
 class hac_exec(C.Structure):
     _fields_ = [("ants_per_warp", C.c_int32), ("warps_per_block", C.c_int32),
                 ("use_graph", C.c_int32), ("fused", C.c_int32), ("fallback_list", C.c_int32),
-                ("profile", C.c_int32), ("cluster_log2", C.c_int32)]
+                ("profile", C.c_int32), ("cluster_log2", C.c_int32), ("parts", C.c_int32)]
 
 
 class hac_stats(C.Structure):
@@ -198,8 +198,8 @@ def to_c_params(p) -> hac_params:
 
 
 def make_exec(ants_per_warp=0, warps_per_block=0, use_graph=1, fused=0, fallback_list=0, profile=0,
-              cluster_log2=0):
-    return hac_exec(ants_per_warp, warps_per_block, use_graph, fused, fallback_list, profile, cluster_log2)
+              cluster_log2=0, parts=0):
+    return hac_exec(ants_per_warp, warps_per_block, use_graph, fused, fallback_list, profile, cluster_log2, parts)
 
 
 # ------------------------------------------------------------------ C-named calls

@@ -184,6 +184,9 @@ def test_mixed_batch_parity(hac, orc):
             insts.append(synth.euclid_instance(40 + b, n, K=20))
             ps.append(params(m=m, k=k, iterations=5 + b, rho=0.2, local_search=ls, seed=100 + b))
     run_case(hac, orc, insts, ps)
+    # the per-step kernels with the instances split into parts on their own streams
+    for parts, apw, graph in ((2, 4, 1), (3, 16, 0), (5, 1, 1)):
+        run_case(hac, orc, insts, ps, exec_=hac.make_exec(apw, 4, graph, fallback_list=32, parts=parts))
 
 
 def test_iterate_in_steps_equals_run(hac, orc):
