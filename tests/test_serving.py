@@ -45,8 +45,11 @@ def _requests():
     return reqs
 
 
-def _drain(srv, tickets, out, max_ticks=1000):
-    for _ in range(max_ticks):
+def _drain(srv, tickets, out, max_ticks=1000, max_seconds=120.0):
+    import time
+    t0 = time.perf_counter()
+    ticks = 0
+    while ticks < max_ticks or time.perf_counter() - t0 < max_seconds:
         for t in list(tickets):
             res = srv.poll(t)
             if res is not None:
@@ -55,6 +58,9 @@ def _drain(srv, tickets, out, max_ticks=1000):
         if not tickets:
             return
         srv.tick()
+        ticks += 1
+        if ticks >= max_ticks:
+            time.sleep(0.001)     # a large request may still be in its preparation
     raise AssertionError("requests did not finish")
 
 
