@@ -55,3 +55,49 @@ def test_two_ranks_shard_instances_and_combine_timing():
 def test_combine_without_a_group_is_identity():
     import bench
     assert bench.combine_ranks([3.5, 7.0], "cpu", ["max", "sum"]) == [3.5, 7.0]
+
+
+def _decode_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import dataclasses
+
+        import bench
+        from oracle import oracle as orc
+        insts, ps = bench.workload("batch128", rank, count=1)
+        p = dataclasses.replace(ps[0], m=8, iterations=2)
+        o = orc.Oracle(insts[0], p).iterate(2)
+        mine = (p.seed, float(o.scalars()["L_gb"]))
+        gathered = [None] * world
+        dist.all_gather_object(gathered, mine)      # host-side gather of (seed, L_gb) per rank
+        out[rank] = gathered
+    finally:
+        dist.destroy_process_group()
+
+
+def test_each_rank_decodes_its_own_shard():
+    """Two gloo ranks each decode their own instance (the CPU oracle stands in
+    for the GPU decode here); the gathered results equal decoding the same
+    instances in one process, so the shards are independent."""
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_decode_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(300)
+            assert p.exitcode == 0
+        g0, g1 = list(out[0]), list(out[1])
+    assert g0 == g1
+    import dataclasses
+
+    import bench
+    from oracle import oracle as orc
+    for rank, (seed, L) in enumerate(g0):
+        insts, ps = bench.workload("batch128", rank, count=1)
+        assert ps[0].seed == seed
+        p = dataclasses.replace(ps[0], m=8, iterations=2)
+        assert orc.Oracle(insts[0], p).iterate(2).scalars()["L_gb"] == L
