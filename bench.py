@@ -71,6 +71,10 @@ def parse():
     ap.add_argument("--wpb", type=int, default=0, help="construction warps per block")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--side", type=int, default=-1,
+                    help="1: after the batch128 line's own measurement, time the other workloads (tsp500, "
+                         "atsp1000, tsp10k_2opt, serve) in subprocesses and attach their summaries; "
+                         "-1 (default): on for the autotuned full batch128 run at N=1")
     ap.add_argument("--cpu-sample", type=int, default=16, help="instances in the CPU sample")
     ap.add_argument("--cpu-iters", type=int, default=20, help="iterations in the CPU sample")
     ap.add_argument("--count", type=int, default=0, help="use only the first COUNT instances (profiling)")
@@ -343,6 +347,64 @@ def input_bytes(insts):
     return int(tot)
 
 
+# the other workloads, each timed by its own bench.py process after the
+# default one (so that one default run records every configuration): the
+# arguments fix the layout the autotuner picks for tsp10k_2opt, whose
+# autotuning alone takes a minute
+SIDE_RUNS = (
+    ("tsp500", ["--steps", "5", "--warmup", "3", "--no-cpu"]),
+    ("atsp1000", ["--steps", "3", "--warmup", "3", "--no-cpu"]),
+    ("tsp10k_2opt", ["--steps", "1", "--warmup", "3", "--no-cpu", "--no-e2e", "--plain-sample", "1",
+                     "--autotune", "0", "--fused", "0", "--apw", "1", "--wpb", "8", "--parts", "4"]),
+    ("serve", ["--requests", "120", "--warmup", "3"]),
+)
+
+
+def _side_summary(d):
+    """The figures of one workload's line that the default line carries."""
+    keep = {k: d.get(k) for k in ("value", "unit", "ms_per_step", "steps", "warmup", "instances_per_s",
+                                  "ant_steps_per_s", "gpu_launches", "device_error")
+            if d.get(k) is not None}
+    cfg = d.get("config", {})
+    keep["layout"] = {k: cfg.get(k) for k in ("ants_per_warp", "fused", "cluster_log2", "fallback_list",
+                                              "warps_per_block", "parts") if k in cfg}
+    if d.get("roofline"):
+        keep["roofline"] = {k: d["roofline"].get(k) for k in ("kernel", "achieved", "peak", "unit", "frac")}
+    if d.get("e2e"):
+        keep["e2e"] = {k: d["e2e"].get(k) for k in ("value", "unit")}
+    if d.get("plain_gpu"):
+        pg = d["plain_gpu"]
+        keep["plain_gpu"] = {k: pg.get(k) for k in ("value", "unit", "speedup_of_batched", "p50_ms", "p99_ms",
+                                                     "instances_per_s", "server_p50_ms_same_requests",
+                                                     "server_p99_ms_same_requests", "requests") if k in pg}
+    if d.get("latency_ms"):
+        keep["latency_ms"] = {k: d["latency_ms"].get(k) for k in ("p50", "p90", "p99")}
+    if d.get("latency_model"):
+        keep["critical_share"] = d["latency_model"].get("critical_share")
+    if d.get("clocks"):
+        keep["clocks"] = {k: d["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    return keep
+
+
+def side_configs():
+    out = {}
+    for name, extra in SIDE_RUNS:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name] + extra
+        t0 = time.perf_counter()
+        r = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, timeout=900,
+                           env={k: v for k, v in os.environ.items()
+                                if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT")})
+        entry = {"command": "python bench.py --workload " + name + " " + " ".join(extra),
+                 "wall_s": time.perf_counter() - t0, "rc": r.returncode}
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode == 0 and lines:
+            entry.update(_side_summary(json.loads(lines[-1])))
+        else:
+            entry["error"] = (r.stderr or r.stdout).strip().splitlines()[-1:] or ["no output"]
+        out[name] = entry
+    return out
+
+
 def run_ours(args):
     import ctypes as C
 
@@ -560,6 +622,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = _cpu_block(oracle_sample(insts, ps, args.cpu_sample, args.cpu_iters))
 
+    side = None
+    if args.side == 1 or (args.side == -1 and args.workload == "batch128" and world == 1 and args.autotune
+                          and not args.count and not args.uniform_n and not args.iters):
+        side = side_configs()
+
     if rank == 0:
         line = {
             "metric": "ant-steps/s", "value": value, "unit": "ant-steps/s", "n_gpus": world,
@@ -593,6 +660,8 @@ def run_ours(args):
             "gpu_launches": stats["launches"],
             "wall_s": wall,
         }
+        if side is not None:
+            line["other_configs"] = side
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
