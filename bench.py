@@ -638,8 +638,9 @@ def run_ours(args):
                        "parallelism": f"instance batches, one per GPU ({world})",
                        "l2": "256 MiB buffer written between timed steps (L2 is 129 MB)",
                        "inputs": "resident in HBM before the timed region",
-                       "ants_per_warp": (ex.ants_per_warp or ("per instance: 4 on one CTA, else 2 on a cluster"
-                                                               if args.fused else 4)), "fused": args.fused,
+                       "ants_per_warp": (ex.ants_per_warp or
+                                         ("per instance: 4 on one CTA where table, masks and coordinates fit, "
+                                          "else 2 on a cluster" if args.fused else 4)), "fused": args.fused,
                        "warps_per_block": args.wpb, "cluster_log2": args.clog, "parts": args.parts,
                        "uniform_n": args.uniform_n or None,
                        "fallback_list": args.fbl, "autotune": tune,

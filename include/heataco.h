@@ -135,7 +135,9 @@ typedef struct {
 /* Execution options of a batch (none of them changes any result). */
 typedef struct {
     int32_t ants_per_warp;    /* 1, 2 or 4 ants share one warp (8-lane segments), 16 (one ant per
-                                 lane pair) or 32 (one ant per lane); 0 = auto */
+                                 lane pair) or 32 (one ant per lane); 0 = auto (fused: per
+                                 instance, 4 on one CTA when its table, visited masks and
+                                 coordinates fit in one SM's shared memory, else 2 on a cluster) */
     int32_t warps_per_block;  /* construction block size in warps; 0 = auto */
     int32_t use_graph;        /* 1: capture the iteration loop (per-step kernels: 10 iterations
                                  per graph; fused: the concurrent group launches) in a CUDA

@@ -348,11 +348,15 @@ inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &mem
         if (zs[members[q]].n > 65534) return HAC_EUNSUPPORTED;
         int rows, warps;
         if (apw == 0) {
-            // one CTA only when its coordinates and lookup lists fit beside the table too
+            // one CTA (one SM) whenever the table, the visited masks and the
+            // coordinates of the fallback scan fit; the lookup lists then stay
+            // in global memory unless the group's CTAs have room for them.
+            // One SM per instance instead of a cluster of two frees SMs for
+            // the rest of the batch, whose makespan is otherwise bound by the
+            // SM time of the clusters rather than by its longest instance.
             const Sizes &z = zs[members[q]];
             if (clog_min == 0 && fits(q, 0, 4, rows, warps) &&
-                fused_smem_bytes(rows, z.kp, warps, 4, (z.n + 32) / 32, z.n, fallback_list ? rows : 0) <=
-                    FUSED_SMEM_LIMIT) {
+                fused_smem_bytes(rows, z.kp, warps, 4, (z.n + 32) / 32, z.n, 0) <= FUSED_SMEM_LIMIT) {
                 clog[q] = 0;
                 qapw[q] = 4;
                 continue;

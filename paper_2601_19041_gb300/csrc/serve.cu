@@ -218,6 +218,7 @@ int tick_iters(const hac_server *sv, const Slot &S)
 int enqueue_groups(hac_server *sv, std::vector<FusedGroup> &groups, const int32_t *d_order,
                    const int32_t *d_iters)
 {
+    if (groups.size() > 4) return HAC_EUNSUPPORTED;   // one stream per cluster size
     for (size_t g = 1; g < groups.size(); ++g) {
         groups[g].side = sv->side[g - 1];
         groups[g].fork = sv->fork[g - 1];

@@ -161,7 +161,10 @@ def test_fused_kernel_parity(hac, orc, name, cfg):
 def test_fused_mixed_batch_groups(hac, orc):
     # different sizes land in different cluster-size groups that run concurrently
     insts, ps = [], []
-    for b, (n, k, m) in enumerate([(90, 20, 9), (1900, 20, 40), (4000, 12, 20), (333, 10, 17), (12, 8, 5)]):
+    # n = 1400 fits one CTA only without its lookup lists: the one-CTA group then
+    # reads every member's lists from global memory
+    for b, (n, k, m) in enumerate([(90, 20, 9), (1900, 20, 40), (4000, 12, 20), (333, 10, 17), (12, 8, 5),
+                                   (1400, 20, 24)]):
         insts.append(synth.euclid_instance(70 + b, n, K=20))
         ps.append(params(m=m, k=k, iterations=3 + b, rho=0.2, seed=170 + b))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(4, 0, 1, fused=1, fallback_list=32))
@@ -169,8 +172,10 @@ def test_fused_mixed_batch_groups(hac, orc):
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(16, 0, 1, fused=1, fallback_list=32))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(32, 4, 1, fused=0, fallback_list=32))
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(16, 4, 1, fused=0, fallback_list=32))
-    # ants per warp chosen per instance: 4 on one CTA where it fits, else 2 on a cluster
+    # ants per warp chosen per instance: 4 on one CTA where the table, masks and
+    # coordinates fit, else 2 on a cluster
     run_case(hac, orc, insts, ps, exec_=hac.make_exec(0, 0, 1, fused=1, fallback_list=32))
+    run_case(hac, orc, insts, ps, exec_=hac.make_exec(0, 0, 1, fused=1, fallback_list=0))
 
 
 def test_mixed_batch_parity(hac, orc):
