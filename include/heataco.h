@@ -217,11 +217,18 @@ int hac_batch_sync(hac_batch *bt);
  *   NBR    int32  n*ls_k    geometric 2-opt neighbour lists
  *   TRACE  f64    5*I       per iteration: ib ant, L_ib, L_gb, L_rb (+inf when
  *                           cleared), code (1: T_rb deposited, 2: restart)
+ *   FBL    int32  n*32      nearest-unvisited lookup list of node i: the nodes
+ *                           u != i (not in C_i when every candidate's choice
+ *                           value stays positive) by (FP32 key, u), -1 past
+ *                           the end; HAC_EINVAL when the exec has no lists
+ *   FBL2   uint16 n*256     the next 256 nodes of the same order (ranks
+ *                           32..287), 0xffff past the end; HAC_EINVAL when
+ *                           absent (no lists, or n > 65535)
  * The call synchronises the stream. */
 enum hac_field {
     HAC_F_CAND = 1, HAC_F_CDIST, HAC_F_CONF, HAC_F_BASE, HAC_F_EVID, HAC_F_W, HAC_F_TAU,
     HAC_F_CHOICE, HAC_F_NN_TOUR, HAC_F_GB_TOUR, HAC_F_IB_TOUR, HAC_F_TOURS, HAC_F_LENS,
-    HAC_F_SCALARS, HAC_F_NBR, HAC_F_TRACE
+    HAC_F_SCALARS, HAC_F_NBR, HAC_F_TRACE, HAC_F_FBL, HAC_F_FBL2
 };
 int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size_t bytes);
 

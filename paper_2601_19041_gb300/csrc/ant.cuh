@@ -24,7 +24,7 @@
 namespace hac {
 
 constexpr unsigned FULL_MASK = 0xffffffffu;
-constexpr int FBL = 32;   // fallback list length (nearest nodes in key order)
+constexpr int FBL = FBL1_LEN;   // fallback list length (nearest nodes in key order)
 
 __device__ __forceinline__ uint32_t word_of(const U4 &v, int w)
 {
@@ -148,6 +148,25 @@ struct ClusterList {
         return v == 0xffff ? -1 : (int)v;
     }
 };
+
+// Second-level lookup (whole warp): the next FBL2_LEN nodes of `node`'s key
+// order, 8 per lane in order (lane L holds ranks 32 + 8L .. 32 + 8L + 7).
+// Returns the first one that `visited` reports unvisited, or -1 (then the
+// nearest unvisited node lies further out and the scan finds it).
+template <typename Visited>
+__device__ __forceinline__ int lookup2(const uint16_t *fbl2, int node, int lane, Visited visited)
+{
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(fbl2 + (size_t)node * FBL2_LEN) + lane);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    int first = -1;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const int u = (int)((w[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+        if (u != 0xffff && !visited(u)) first = u;
+    }
+    const unsigned bm = __ballot_sync(FULL_MASK, first >= 0);
+    return bm ? __shfl_sync(FULL_MASK, first, __ffs(bm) - 1) : -1;
+}
 
 // Hillis-Steele inclusive scan (offsets 1, 2, 4) over 8 group totals, of
 // which only the first GT can be non-zero; the exclusive prefix of group g is
@@ -325,6 +344,8 @@ __device__ __forceinline__ void build_tours(const DevInst &I, const Rows &rows, 
                 const bool ok = u >= 0 && !((sv[u >> 5] >> (u & 31)) & 1u);
                 const unsigned bm = __ballot_sync(FULL_MASK, ok);
                 if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
+                if (found < 0 && I.fbl2)
+                    found = lookup2(I.fbl2, scur, lane, [&](int u2) { return (sv[u2 >> 5] >> (u2 & 31)) & 1u; });
             }
             if (found < 0) {
                 float bk = __int_as_float(0x7f800000);

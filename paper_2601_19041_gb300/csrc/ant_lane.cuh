@@ -151,6 +151,9 @@ __device__ __forceinline__ void build_tours_lane(const DevInst &I, const Rows &r
                     const bool ok = u >= 0 && !((vis_warp[(u >> 5) * 32 + L] >> (u & 31)) & 1u);
                     const unsigned bm = __ballot_sync(FULL_MASK, ok);
                     if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
+                    if (found < 0 && I.fbl2)
+                        found = lookup2(I.fbl2, scur, lane,
+                                        [&](int u2) { return (vis_warp[(u2 >> 5) * 32 + L] >> (u2 & 31)) & 1u; });
                 }
                 if (found < 0) {
                     float bk = __int_as_float(0x7f800000);

@@ -174,6 +174,8 @@ __device__ __forceinline__ void build_tours_pair(const DevInst &I, const Rows &r
                 const bool ok = u >= 0 && !((sv[16 * (u >> 5)] >> (u & 31)) & 1u);
                 const unsigned bm = __ballot_sync(FULL_MASK, ok);
                 if (bm) found = __shfl_sync(FULL_MASK, u, __ffs(bm) - 1);
+                if (found < 0 && I.fbl2)
+                    found = lookup2(I.fbl2, scur, lane, [&](int u2) { return (sv[16 * (u2 >> 5)] >> (u2 & 31)) & 1u; });
             }
             if (found < 0) {
                 float bk = __int_as_float(0x7f800000);

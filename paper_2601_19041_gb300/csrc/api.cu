@@ -540,6 +540,12 @@ int hac_batch_read(hac_batch *bt, int32_t b, int32_t field, void *host_dst, size
         if (!D.ls_k) return HAC_EINVAL;
         src = D.nbr; sz = n * D.ls_k * 4; break;
     case HAC_F_TRACE: src = D.trace; sz = (size_t)TRACE_W * std::max(D.iters, 1) * 8; break;
+    case HAC_F_FBL:
+        if (!D.fbl) return HAC_EINVAL;
+        src = D.fbl; sz = n * FBL_LEN * 4; break;
+    case HAC_F_FBL2:
+        if (!D.fbl2) return HAC_EINVAL;
+        src = D.fbl2; sz = n * FBL2_LEN * 2; break;
     case HAC_F_SCALARS: {
         if (bytes < 21 * sizeof(double)) return HAC_EINVAL;
         InstState S0;

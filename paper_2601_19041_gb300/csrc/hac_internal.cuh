@@ -15,6 +15,9 @@
 namespace hac {
 
 constexpr int KMAX = HAC_KMAX;
+constexpr int FBL1_LEN = 32;           // nearest-unvisited lookup list: the 32 first nodes in key order
+constexpr int FBL2_LEN = 256;          // second-level nearest-unvisited list: key-order ranks 32..287
+constexpr int FBL2_SORT = 512;         // its sort buffer (a power of two >= 32 + FBL2_LEN)
 constexpr double DFLOOR = 1e-9;     // eta = 1/max(d, 1e-9): coincident points
 constexpr double LS_GAIN = 1e-10;   // 2-opt moves need a gain above this
 constexpr int TRACE_W = 5;          // trace entries per iteration: ib ant, L_ib, L_gb, L_rb, code
@@ -75,6 +78,7 @@ struct DevInst {
     uint8_t *ls_dlb;          // n, don't-look bits
     int32_t *fbl;             // n*fbl_len (nearest-unvisited lookup list)
     int32_t fbl_len;
+    uint16_t *fbl2;           // n*FBL2_LEN second-level list (the next nodes of the same order), or null
     // search state
     int32_t *nn_tour, *gb_tour, *ib_tour, *succ, *pred;   // n each
     int32_t *rb_tour;         // n, restart-best tour (schedule = 1)

@@ -27,7 +27,7 @@ extern thread_local int g_last_cuda;
 constexpr int ROWS_PER_BLOCK = 8;      // matches the row kernels (8 warps, a row each)
 constexpr int SLOTS_PER_BLOCK = 1024;  // matches the slot kernels
 constexpr int GRAPH_CHUNK = 10;        // iterations per captured graph
-constexpr int FBL_LEN = 32;            // nearest-unvisited lookup list (ant.cuh FBL)
+constexpr int FBL_LEN = FBL1_LEN;      // nearest-unvisited lookup list
 
 struct Arena {
     size_t off = 0;
@@ -176,6 +176,7 @@ void layout_instance(Arena &A, const Sizes &z, int on_dev, F &&put)
         }
     }
     put("fbl", A.take(n * FBL_LEN * 4));
+    put("fbl2", A.take(n * FBL2_LEN * 2));
     put("nn_tour", A.take(n * 4));
     put("gb_tour", A.take(n * 4));
     put("rb_tour", A.take(n * 4));
@@ -291,7 +292,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
         SETP(lsa_pos, int32_t *) SETP(lsa_el, float *) SETP(lsa_dlb, uint8_t *)
         SETP(gb_tour, int32_t *) SETP(ib_tour, int32_t *) SETP(succ, int32_t *) SETP(rb_tour, int32_t *)
         SETP(pred, int32_t *) SETP(tours, int32_t *) SETP(lens, double *) SETP(trace, double *)
-        SETP(fbl, int32_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)
+        SETP(fbl, int32_t *) SETP(fbl2, uint16_t *) SETP(slots, uint8_t *) SETP(dstep, double *) SETP(fbs, int32_t *)
         SETP(fbcnt, int32_t *)
 #undef SETP
         if (!std::strcmp(name, "xy")) D.xy = (const float *)ptr;
@@ -301,6 +302,7 @@ inline void bind_instance(DevInst &D, const hac_instance &in, const hac_params &
         if (!std::strcmp(name, "val")) D.val = ptr;
     });
     if (!ex.fallback_list) D.fbl = nullptr;
+    if (!ex.fallback_list || z.n > 65535) D.fbl2 = nullptr;   // uint16 node ids
     if (ex.ants_per_warp == 32) { D.tour_sa = 1; D.tour_ss = p.m; }   // step-major tours
     else { D.tour_sa = z.n; D.tour_ss = 1; }
     D.fbl_len = ex.fallback_list;

@@ -728,6 +728,141 @@ __global__ void k_fbl(const DevInst *insts, const int2 *rowmap, int words_per_wa
     I.fbl[(size_t)i * 32 + lane] = lane < K ? mine : -1;
 }
 
+// Order-preserving bit pattern of a key: unsigned comparison of the patterns
+// is the float comparison (-0 is taken as +0, as the float compare does).
+__device__ __forceinline__ unsigned ord_key(float k)
+{
+    const unsigned b = __float_as_uint(__fadd_rn(k, 0.0f));
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Second-level list for the fallback of Alg. 2: ranks 32..287 of the order
+// of k_fbl (nodes u != i, not in C_i when that is safe, by (FP32 key, u)),
+// 0xffff past the last node.  When the 32 nearest are all visited, the first
+// unvisited node of this list is the nearest unvisited node, exactly.
+// One warp per row: the key of rank T = min(288, available) by an exact
+// radix selection (four 8-bit digits of ord_key), the nodes below it plus
+// the lowest-index nodes at it, then a bitonic sort of those (key, u) pairs.
+// Shared memory per warp: sort buffer (FBL2_SORT x 8 B) | histogram (256) |
+// exclusion mask (`words_per_warp`, even).
+__global__ void k_fbl2(const DevInst *insts, const int2 *rowmap, int words_per_warp)
+{
+    extern __shared__ unsigned long long fbl2_smem[];
+    const int2 rm = rowmap[blockIdx.x];
+    const DevInst &I = insts[rm.x];
+    if (!I.fbl2) return;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = rm.y + wib;
+    if (i >= I.n) return;
+    unsigned long long *buf = fbl2_smem + (size_t)wib * (FBL2_SORT + (256 + words_per_warp) / 2);
+    unsigned *hist = reinterpret_cast<unsigned *>(buf + FBL2_SORT);
+    unsigned *mask = hist + 256;
+    const int n = I.n, nw = (n + 31) >> 5;
+    for (int w = lane; w < nw; w += 32) mask[w] = 0u;
+    __syncwarp();
+    if (I.st->fbl_unsafe == 0 && lane < I.k_pad) {
+        const int j = I.cand[(size_t)i * I.k_pad + lane];
+        if (j >= 0) atomicOr(&mask[j >> 5], 1u << (j & 31));
+    }
+    if (lane == 0) atomicOr(&mask[i >> 5], 1u << (i & 31));
+    __syncwarp();
+    const float2 *xy = reinterpret_cast<const float2 *>(I.xy);
+    const float2 pi = I.kind == 0 ? xy[i] : make_float2(0.f, 0.f);
+    const float *crow = I.kind == 1 ? I.cost + (size_t)i * n : nullptr;
+    auto okey = [&](int u) { return ord_key(I.kind == 0 ? key32_xy(pi, xy[u]) : crow[u]); };
+    auto live = [&](int u) { return !((mask[u >> 5] >> (u & 31)) & 1u); };
+
+    int avail = 0;
+    for (int w = lane; w < nw; w += 32) {
+        unsigned v = ~mask[w];
+        if (w == nw - 1 && (n & 31)) v &= (1u << (n & 31)) - 1u;
+        avail += __popc(v);
+    }
+    avail = __reduce_add_sync(FULL, avail);
+    const int T = min(avail, FBL1_LEN + FBL2_LEN);
+    uint16_t *out = I.fbl2 + (size_t)i * FBL2_LEN;
+    if (T <= FBL1_LEN) {
+        for (int r = lane; r < FBL2_LEN; r += 32) out[r] = (uint16_t)0xffff;
+        return;
+    }
+
+    // radix selection of the key of rank T (1-based); `need` ends as the
+    // number of nodes taken at that key
+    unsigned prefix = 0u, pmask = 0u;
+    int need = T;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+        __syncwarp();
+        for (int u = lane; u < n; u += 32) {
+            if (!live(u)) continue;
+            const unsigned k = okey(u);
+            if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+        unsigned c[8], tot = 0u;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) { c[b] = hist[8 * lane + b]; tot += c[b]; }
+        unsigned inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const unsigned exc = inc - tot;
+        const unsigned owner = __ballot_sync(FULL, exc < (unsigned)need && (unsigned)need <= inc);
+        const int L = __ffs(owner) - 1;
+        int d = 0;
+        unsigned before = 0u;
+        if (lane == L) {
+            unsigned acc = exc;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                if (acc + c[b] >= (unsigned)need) { d = 8 * lane + b; before = acc; break; }
+                acc += c[b];
+            }
+        }
+        d = __shfl_sync(FULL, d, L);
+        before = __shfl_sync(FULL, before, L);
+        need -= (int)before;
+        prefix |= (unsigned)d << shift;
+        pmask |= 255u << shift;
+        __syncwarp();
+    }
+
+    // the T smallest (key, u): every node below the selected key and the
+    // `need` lowest-index nodes at it, compacted in index order
+    int pos = 0, ties = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int u = base + lane;
+        unsigned k = 0xffffffffu;
+        bool lt = false, eq = false;
+        if (u < n && live(u)) { k = okey(u); lt = k < prefix; eq = k == prefix; }
+        const unsigned below = (1u << lane) - 1u;
+        const unsigned beq = __ballot_sync(FULL, eq);
+        const bool take = lt || (eq && ties + __popc(beq & below) < need);
+        const unsigned bt = __ballot_sync(FULL, take);
+        if (take) buf[pos + __popc(bt & below)] = ((unsigned long long)k << 32) | (unsigned)u;
+        pos += __popc(bt);
+        ties += __popc(beq);
+    }
+    for (int r = pos + lane; r < FBL2_SORT; r += 32) buf[r] = ~0ull;
+    __syncwarp();
+    // bitonic sort, ascending (each element is in exactly one pair per stage)
+    for (int k = 2; k <= FBL2_SORT; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = lane; x < FBL2_SORT; x += 32) {
+                const int y = x ^ j;
+                if (y > x) {
+                    const unsigned long long a = buf[x], b = buf[y];
+                    if ((a > b) == ((x & k) == 0)) { buf[x] = b; buf[y] = a; }
+                }
+            }
+            __syncwarp();
+        }
+    for (int r = lane; r < FBL2_LEN; r += 32)
+        out[r] = r + FBL1_LEN < T ? (uint16_t)(buf[r + FBL1_LEN] & 0xffffu) : (uint16_t)0xffff;
+}
+
 // ------------------------------------------------------------ T_NN
 
 // Nearest-neighbour tour from node 0 (one block per instance): each step takes
@@ -872,8 +1007,13 @@ int launch_prep(const DevInst *d_inst, const DevInst *h_inst, int count, const i
     if (fbl_smem > 48 * 1024)
         cudaFuncSetAttribute(k_fbl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbl_smem);
     k_fbl<<<rowmap_len, threads, fbl_smem, s>>>(d_inst, d_rowmap, wpw);
+    const int wpw2 = ((wpw < 2048 ? wpw : 2048) + 1) & ~1;   // lists of n <= 65535 only
+    const size_t fbl2_smem = (size_t)ROW_WARPS * (FBL2_SORT * 8 + (256 + wpw2) * 4);
+    if (fbl2_smem > 48 * 1024)
+        cudaFuncSetAttribute(k_fbl2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fbl2_smem);
+    k_fbl2<<<rowmap_len, threads, fbl2_smem, s>>>(d_inst, d_rowmap, wpw2);
     k_init_tau<<<slotmap_len, 1024, 0, s>>>(d_inst, d_slotmap);
-    return launched + 5;
+    return launched + 6;
 }
 
 }  // namespace hac

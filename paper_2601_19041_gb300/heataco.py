@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libheataco.so")
 HAC_OK, HAC_EINVAL, HAC_ENOMEM, HAC_ECUDA, HAC_ETIMEOUT, HAC_EUNSUPPORTED, HAC_EBUSY = 0, -1, -2, -3, -4, -5, -6
 
 FIELDS = dict(CAND=1, CDIST=2, CONF=3, BASE=4, EVID=5, W=6, TAU=7, CHOICE=8, NN_TOUR=9,
-              GB_TOUR=10, IB_TOUR=11, TOURS=12, LENS=13, SCALARS=14, NBR=15, TRACE=16)
+              GB_TOUR=10, IB_TOUR=11, TOURS=12, LENS=13, SCALARS=14, NBR=15, TRACE=16, FBL=17, FBL2=18)
 SCALAR_KEYS = ("q90", "Rhat", "kappa", "p_x", "L_nn", "tau_max64", "tau_min64", "tau_max",
                "tau_min", "L_gb", "L_ib", "n_lambda", "t", "ib", "n_fallback", "k_pad", "L_rb", "n_restarts",
                "t_restart", "u_gb", "edges_per_n")
@@ -293,6 +293,7 @@ class Batch:
             "TOURS": (np.int32, (m, n)), "LENS": (np.float64, (m,)),
             "SCALARS": (np.float64, (21,)), "NBR": (np.int32, (n, p.ls_k)),
             "TRACE": (np.float64, (max(p.iterations, 1), 5)),
+            "FBL": (np.int32, (n, 32)), "FBL2": (np.uint16, (n, 256)),
         }[field]
 
     def read(self, b: int, field: str):
