@@ -109,14 +109,14 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-# DRAM bytes per fused launch measured with ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) for a workload and layout; the summary with its
-# command is in profiles/dram_traffic_batch128_n500-2000.md.  Reported as
-# roofline.traffic only for the same workload and layout (2 ants per warp
-# puts every instance of this workload on clusters of 2 CTAs, so a smallest
-# cluster of 1 or 2 is the same launch).
-_T_APW2 = 5.542512128e9 + 6.347278080e9
-NCU_TRAFFIC = {("batch128", 1, 2, 32, 0, 200): _T_APW2, ("batch128", 1, 2, 32, 1, 200): _T_APW2}
+# DRAM bytes per step of the fused launches measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of the step's concurrent group
+# launches) for a workload and layout; the ncu summary of the default
+# workload under profiles/ gives the command.  Reported as roofline.traffic
+# only for the same workload and layout: the per-instance layout
+# (ants_per_warp 0) with lookup lists, smallest cluster 1.
+_T_PER_INSTANCE = (0.580602368e9 + 0.929919744e9) + (6.563235072e9 + 3.709806848e9)
+NCU_TRAFFIC = {("batch128", 1, 0, 32, 0, 200): _T_PER_INSTANCE}
 
 
 def load_peaks():
