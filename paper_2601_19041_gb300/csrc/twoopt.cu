@@ -5,14 +5,24 @@
 
 namespace hac {
 
+// One block of LS_WARPS warps per instance: warp 0 runs the search, the other
+// warps help with its long segment reversals and wide pre-tests (twoopt.cuh,
+// 2-opt of symmetric instances) and are released when it ends.
+constexpr int LS_WARPS = 4;   // at most LS_WARPS_MAX
+
 __global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char ls_sm[];
+    __shared__ int coop[LS_COOP_WORDS];
     const DevInst &I = insts[blockIdx.x];
-    if (!I.local_search) return;
-    const LsMem M = ls_shared(I, I.nn_tour, ls_sm, smem_bytes, ls_global(I, I.nn_tour));
+    if (!I.local_search) return;   // the same for the whole block
+    const bool w0 = threadIdx.x < 32;
+    LsMem M = ls_shared(I, I.nn_tour, ls_sm, smem_bytes, ls_global(I, I.nn_tour), w0);
+    if (blockDim.x > 32) { M.coop = coop; M.coop_warps = (int)(blockDim.x >> 5); }
+    if (!w0) { ls_coop_help(I, M); return; }
     if (I.local_search >= 3) warp_three_opt(I, I.nn_tour, M);
     else warp_two_opt_any(I, I.nn_tour, M);
+    ls_coop_end(M);
     const double L = warp_tour_length(I, I.nn_tour);
     if (threadIdx.x == 0) I.st->L_nn = L;
 }
@@ -20,11 +30,16 @@ __global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
 __global__ void k_two_opt_ib(const DevInst *insts, unsigned smem_bytes)
 {
     extern __shared__ __align__(16) unsigned char ls_sm[];
+    __shared__ int coop[LS_COOP_WORDS];
     const DevInst &I = insts[blockIdx.x];
-    if ((I.local_search != 1 && I.local_search != 3) || !I.st->active) return;
-    const LsMem M = ls_shared(I, I.ib_tour, ls_sm, smem_bytes, ls_global(I, I.ib_tour));
+    if ((I.local_search != 1 && I.local_search != 3) || !I.st->active) return;   // the same for the whole block
+    const bool w0 = threadIdx.x < 32;
+    LsMem M = ls_shared(I, I.ib_tour, ls_sm, smem_bytes, ls_global(I, I.ib_tour), w0);
+    if (blockDim.x > 32) { M.coop = coop; M.coop_warps = (int)(blockDim.x >> 5); }
+    if (!w0) { ls_coop_help(I, M); return; }
     if (I.local_search == 3) warp_three_opt(I, I.ib_tour, M);
     else warp_two_opt_any(I, I.ib_tour, M);
+    ls_coop_end(M);
     const double L = warp_tour_length(I, I.ib_tour);
     if (threadIdx.x == 0) I.st->L_ib = L;
 }
@@ -59,7 +74,7 @@ static void ls_launch(Kern kern, const DevInst *d_inst, int count, int max_n, cu
 {
     const size_t smem = ls_launch_smem(max_n);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<count, 32, smem, s>>>(d_inst, (unsigned)smem);
+    kern<<<count, 32 * LS_WARPS, smem, s>>>(d_inst, (unsigned)smem);
 }
 
 void launch_two_opt_all(const DevInst *d_inst, int count, int max_m, int max_n, cudaStream_t s)

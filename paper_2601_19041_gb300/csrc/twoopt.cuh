@@ -66,7 +66,31 @@ struct LsMem {
     uint8_t *dlb;       // don't-look bit by city
     float *el;          // el[p] ~ d(tour[p], tour[p+1 mod n]), FP32
     const float2 *xy;   // coordinates
+    int *coop = nullptr;   // shared command words of the helper warps (null: warp 0 alone)
+    int coop_warps = 1;    // warps of the block (warp 0 searches, the others help)
 };
+
+// Helper warps.  The search is sequential and runs in warp 0; in a block of
+// several warps the others wait at named barrier 1 and take their share of
+// each long segment reversal (its element pairs are independent, so the
+// result does not depend on who swaps which pair).  Protocol, per reversal:
+// warp 0 writes {1, i0, len} to coop, both sides arrive at the barrier, swap
+// their pairs, and arrive again; at the end warp 0 writes {0} and arrives
+// once.  Every path through the search ends with that final arrival.
+constexpr int LS_COOP_LEN = 192;   // reversals of at least this many positions are shared
+// The FP32 pre-test of 32 positions (ls_first_may_move) is shared too when it
+// has more than 32 work items: warp 0 stages its 32 cities and the item counts,
+// and the block deals the items 32 * warps at a time (command 2).
+// coop words: [0] command (0 exit, 1 reverse, 2 pre-test), [1] i0 or item
+// count, [2] len; from LS_ST the staged cities (al, an0, an1, c0, incl, da0,
+// da1; 32 each); from LS_MIN the per-warp minima of two rounds (2 x 8)
+constexpr int LS_ST = 8, LS_MIN = LS_ST + 7 * 32, LS_COOP_WORDS = LS_MIN + 16;
+constexpr int LS_WARPS_MAX = 8;
+
+__device__ __forceinline__ void ls_coop_bar(int warps)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * warps) : "memory");
+}
 
 __device__ __forceinline__ float ls_d32(const float2 *xy, int u, int v)
 {
@@ -92,29 +116,17 @@ __device__ __forceinline__ bool ls_may_improve(float da, float dab, float dbb, f
     return ls_gain_class(da, dab, dbb, dn) != 0;
 }
 
-// reverse so that (x, succ x), (y, succ y) become (x, y), (succ x, succ y);
-// the inner edges of the reversed range swap, the two new edges get dxy, dss
-__device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, int y, float dxy, float dss)
+// the element swaps of reversing positions i0 .. i0+len-1 (mod n) that fall to
+// thread `tid` of `nth`: tour/pos pairs and the inner edge lengths; the pairs
+// of different t are disjoint, so each thread loads two pairs before it
+// stores them
+__device__ __forceinline__ void ls_reverse_part(const LsMem &M, int n, int i0, int len, int tid, int nth)
 {
-    const int lane = threadIdx.x & 31;
-    int i0 = wrap_next(M.pos[x], n);
-    int len = M.pos[y] - i0;
-    if (len < 0) len += n;
-    len += 1;
-    if (2 * len > n) {
-        i0 = wrap_next(M.pos[y], n);
-        len = M.pos[x] - i0;
-        if (len < 0) len += n;
-        len += 1;
-    }
-    __syncwarp();
-    // the pairs (p, q) of different t are disjoint, so each lane loads two
-    // pairs before it stores them
     const int h = len / 2;
-    for (int t = lane; t < h; t += 64) {
-        const bool two = t + 32 < h;
+    for (int t = tid; t < h; t += 2 * nth) {
+        const bool two = t + nth < h;
         int p0 = i0 + t, q0 = i0 + len - 1 - t;
-        int p1 = p0 + 32, q1 = q0 - 32;
+        int p1 = p0 + nth, q1 = q0 - nth;
         if (p0 >= n) p0 -= n;
         if (q0 >= n) q0 -= n;
         if (p1 >= n) p1 -= n;
@@ -133,10 +145,10 @@ __device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, in
         }
     }
     const int he = (len - 1) / 2;
-    for (int t = lane; t < he; t += 64) {
-        const bool two = t + 32 < he;
+    for (int t = tid; t < he; t += 2 * nth) {
+        const bool two = t + nth < he;
         int p0 = i0 + t, q0 = i0 + len - 2 - t;
-        int p1 = p0 + 32, q1 = q0 - 32;
+        int p1 = p0 + nth, q1 = q0 - nth;
         if (p0 >= n) p0 -= n;
         if (q0 >= n) q0 -= n;
         if (p1 >= n) p1 -= n;
@@ -149,6 +161,109 @@ __device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, in
             M.el[p1] = v1;
             M.el[q1] = u1;
         }
+    }
+}
+
+// One pre-test work item: candidate move of city a in direction dir (0: succ,
+// 1: pred) with its q-th neighbour; true unless the FP64 gain is certainly
+// <= LS_GAIN.  an, da: the city's dir-neighbour and FP32 edge length.
+__device__ __forceinline__ bool ls_item_may_improve(const DevInst &I, const LsMem &M, int n, int K, int a, int dir,
+                                                   int q, int an, float da)
+{
+    const int b = I.nbr[(size_t)a * K + q];
+    const float dab = I.nbrd32[(size_t)a * K + q];
+    const int pb = M.pos[b];
+    const int pe = dir == 0 ? pb : wrap_prev(pb, n);     // the edge (b, dir b)
+    const int bn = M.tour[dir == 0 ? wrap_next(pb, n) : pe];
+    return b != an && bn != a && ls_may_improve(da, dab, M.el[pe], ls_d32(M.xy, an, bn));
+}
+
+// The block's side of a shared pre-test (every thread of the block): items
+// t = tid, tid + 32*warps, ... of the staged cities, in rounds; the first
+// round with a possible move gives the answer (the smallest staged lane that
+// owns one), as in the warp's own loop.  All threads return the same value.
+__device__ __forceinline__ int ls_pretest_rounds(const DevInst &I, const LsMem &M, int n, int K, int total)
+{
+    const int *st = M.coop + LS_ST;
+    const int *s_al = st, *s_an0 = st + 32, *s_an1 = st + 64, *s_c0 = st + 96, *s_incl = st + 128;
+    const float *s_da0 = reinterpret_cast<const float *>(st + 160), *s_da1 = reinterpret_cast<const float *>(st + 192);
+    int *mins = M.coop + LS_MIN;
+    const int tid = (int)threadIdx.x, nth = 32 * M.coop_warps, w = tid >> 5;
+    for (int base = 0, r = 0; base < total; base += nth, ++r) {
+        const int t = base + tid;
+        int c = 0;
+        bool hit = false;
+        if (t < total) {
+#pragma unroll
+            for (int s2 = 16; s2 >= 1; s2 >>= 1)
+                if (s_incl[c + s2 - 1] <= t) c += s2;
+            const int j = t - (c ? s_incl[c - 1] : 0);
+            const int cc0 = s_c0[c];
+            const int dir = j < cc0 ? 0 : 1;
+            hit = ls_item_may_improve(I, M, n, K, s_al[c], dir, dir == 0 ? j : j - cc0,
+                                      dir == 0 ? s_an0[c] : s_an1[c], dir == 0 ? s_da0[c] : s_da1[c]);
+        }
+        const unsigned wmin = __reduce_min_sync(FULL2, hit ? (unsigned)c : 32u);
+        if ((tid & 31) == 0) mins[(r & 1) * 8 + w] = (int)wmin;
+        ls_coop_bar(M.coop_warps);
+        int first = 32;
+        for (int q = 0; q < M.coop_warps; ++q) first = min(first, mins[(r & 1) * 8 + q]);
+        if (first < 32) return first;
+    }
+    return 32;
+}
+
+// the helper warps' side of the protocol above (warps 1 .. coop_warps-1)
+__device__ __forceinline__ void ls_coop_help(const DevInst &I, const LsMem &M)
+{
+    const int n = I.n, nth = 32 * M.coop_warps;
+    for (;;) {
+        ls_coop_bar(M.coop_warps);
+        const int cmd = M.coop[0];
+        if (cmd == 1) {
+            ls_reverse_part(M, n, M.coop[1], M.coop[2], (int)threadIdx.x, nth);
+            ls_coop_bar(M.coop_warps);
+        } else if (cmd == 2) {
+            ls_pretest_rounds(I, M, n, I.ls_k, M.coop[1]);
+        } else {
+            break;
+        }
+    }
+}
+
+// warp 0: releases the helper warps (the final arrival of the protocol)
+__device__ __forceinline__ void ls_coop_end(const LsMem &M)
+{
+    if (!M.coop) return;
+    if ((threadIdx.x & 31) == 0) M.coop[0] = 0;
+    __syncwarp();
+    ls_coop_bar(M.coop_warps);
+}
+
+// reverse so that (x, succ x), (y, succ y) become (x, y), (succ x, succ y);
+// the inner edges of the reversed range swap, the two new edges get dxy, dss
+__device__ __forceinline__ void apply_succ_move(const LsMem &M, int n, int x, int y, float dxy, float dss)
+{
+    const int lane = threadIdx.x & 31;
+    int i0 = wrap_next(M.pos[x], n);
+    int len = M.pos[y] - i0;
+    if (len < 0) len += n;
+    len += 1;
+    if (2 * len > n) {
+        i0 = wrap_next(M.pos[y], n);
+        len = M.pos[x] - i0;
+        if (len < 0) len += n;
+        len += 1;
+    }
+    __syncwarp();
+    if (M.coop && len >= LS_COOP_LEN) {
+        if (lane == 0) { M.coop[0] = 1; M.coop[1] = i0; M.coop[2] = len; }
+        __syncwarp();
+        ls_coop_bar(M.coop_warps);
+        ls_reverse_part(M, n, i0, len, lane, 32 * M.coop_warps);
+        ls_coop_bar(M.coop_warps);
+    } else {
+        ls_reverse_part(M, n, i0, len, lane, 32);
     }
     __syncwarp();
     if (lane == 0) {
@@ -204,6 +319,20 @@ __device__ __forceinline__ int ls_first_may_move(const DevInst &I, const LsMem &
     }
     const int excl = incl - cnt;
     const int total = __shfl_sync(FULL2, incl, 31);
+    if (M.coop && total > 32) {    // more than one round: shared with the helper warps
+        int *st = M.coop + LS_ST;
+        st[lane] = al;
+        st[32 + lane] = an0;
+        st[64 + lane] = an1;
+        st[96 + lane] = c0;
+        st[128 + lane] = incl;
+        st[160 + lane] = __float_as_int(da0);
+        st[192 + lane] = __float_as_int(da1);
+        if (lane == 0) { M.coop[0] = 2; M.coop[1] = total; }
+        __syncwarp();
+        ls_coop_bar(M.coop_warps);
+        return ls_pretest_rounds(I, M, n, K, total);
+    }
     for (int base = 0; base < total; base += 32) {
         const int t = base + lane;
         int c = 0;      // the lane whose city owns item t: the number of lanes with incl <= t
@@ -218,15 +347,8 @@ __device__ __forceinline__ int ls_first_may_move(const DevInst &I, const LsMem &
         bool hit = false;
         if (t < total) {
             const int dir = j < cc0 ? 0 : 1;
-            const int q = dir == 0 ? j : j - cc0;
-            const int an = dir == 0 ? xan0 : xan1;
-            const float da = dir == 0 ? xda0 : xda1;
-            const int b = I.nbr[(size_t)a * K + q];
-            const float dab = I.nbrd32[(size_t)a * K + q];
-            const int pb = M.pos[b];
-            const int pe = dir == 0 ? pb : wrap_prev(pb, n);     // the edge (b, dir b)
-            const int bn = M.tour[dir == 0 ? wrap_next(pb, n) : pe];
-            if (b != an && bn != a) hit = ls_may_improve(da, dab, M.el[pe], ls_d32(M.xy, an, bn));
+            hit = ls_item_may_improve(I, M, n, K, a, dir, dir == 0 ? j : j - cc0, dir == 0 ? xan0 : xan1,
+                                      dir == 0 ? xda0 : xda1);
         }
         const unsigned first = __reduce_min_sync(FULL2, hit ? (unsigned)c : 32u);
         if (first < 32u) return (int)first;
@@ -386,8 +508,10 @@ __host__ __device__ inline size_t ls_xy_offset(int n) { return ((size_t)n * 13 +
 __host__ __device__ inline size_t ls_smem_full(int n) { return ls_xy_offset(n) + (size_t)n * 8; }
 
 // arrays in `sm` (smem_bytes) where they fit, else `fallback`; one warp
+// (copy = false: the same pointers without filling the coordinates, for the
+// helper warps of a block)
 __device__ __forceinline__ LsMem ls_shared(const DevInst &I, int32_t *tour, unsigned char *sm, size_t smem_bytes,
-                                           const LsMem &fallback)
+                                           const LsMem &fallback, bool copy = true)
 {
     const int n = I.n;
     if (ls_smem_core(n) > smem_bytes) return fallback;
@@ -399,8 +523,10 @@ __device__ __forceinline__ LsMem ls_shared(const DevInst &I, int32_t *tour, unsi
     M.xy = reinterpret_cast<const float2 *>(I.xy);
     if (I.kind == 0 && ls_smem_full(n) <= smem_bytes) {
         float2 *sxy = reinterpret_cast<float2 *>(sm + ls_xy_offset(n));
-        for (int p = threadIdx.x & 31; p < n; p += 32) sxy[p] = reinterpret_cast<const float2 *>(I.xy)[p];
-        __syncwarp();
+        if (copy) {
+            for (int p = threadIdx.x & 31; p < n; p += 32) sxy[p] = reinterpret_cast<const float2 *>(I.xy)[p];
+            __syncwarp();
+        }
         M.xy = sxy;
     }
     return M;
