@@ -684,16 +684,17 @@ __global__ void k_fbl_check(const DevInst *insts, const int2 *slotmap)
     if (I.cand[s] >= 0 && !(__fmul_rn(I.st->tau_min, I.W[s]) > 0.0f)) I.st->fbl_unsafe = 1;
 }
 
-// For the fallback of Alg. 2: the 32 nodes u != i (not in C_i when that is
-// safe, see k_fbl_check) with the smallest (FP32 key, u), ascending, -1 when
-// fewer exist.  If one of them is unvisited at a fallback, the first unvisited
+// For the fallback of Alg. 2 (instances without a second-level list, n >
+// 65535): the 32 nodes u != i (not in C_i when that is safe, see
+// k_fbl_check) with the smallest (FP32 key, u), ascending, -1 when fewer
+// exist.  If one of them is unvisited at a fallback, the first unvisited
 // one is the nearest unvisited node, exactly.
 __global__ void k_fbl(const DevInst *insts, const int2 *rowmap, int words_per_warp)
 {
     extern __shared__ unsigned int excl_mask[];
     int2 rm = rowmap[blockIdx.x];
     const DevInst &I = insts[rm.x];
-    if (!I.fbl) return;
+    if (!I.fbl || I.fbl2) return;   // with a second-level list, k_fbl2 writes both
     const int i = rm.y + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (i >= I.n) return;
     unsigned *mask = excl_mask + (size_t)(threadIdx.x / 32) * words_per_warp;
@@ -736,10 +737,12 @@ __device__ __forceinline__ unsigned ord_key(float k)
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// Second-level list for the fallback of Alg. 2: ranks 32..287 of the order
-// of k_fbl (nodes u != i, not in C_i when that is safe, by (FP32 key, u)),
-// 0xffff past the last node.  When the 32 nearest are all visited, the first
-// unvisited node of this list is the nearest unvisited node, exactly.
+// Both lookup lists for the fallback of Alg. 2 (instances of n <= 65535):
+// ranks 0..31 of the order of k_fbl (nodes u != i, not in C_i when that is
+// safe, by (FP32 key, u)) into fbl, -1 past the last node, and ranks 32..287
+// into the second-level list, 0xffff past the last node.  When the 32 nearest
+// are all visited, the first unvisited node of the second list is the
+// nearest unvisited node, exactly.
 // One warp per row: the key of rank T = min(288, available) by an exact
 // radix selection (four 8-bit digits of ord_key), the nodes below it plus
 // the lowest-index nodes at it, then a bitonic sort of those (key, u) pairs.
@@ -781,7 +784,9 @@ __global__ void k_fbl2(const DevInst *insts, const int2 *rowmap, int words_per_w
     avail = __reduce_add_sync(FULL, avail);
     const int T = min(avail, FBL1_LEN + FBL2_LEN);
     uint16_t *out = I.fbl2 + (size_t)i * FBL2_LEN;
-    if (T <= FBL1_LEN) {
+    int32_t *out1 = I.fbl + (size_t)i * FBL1_LEN;
+    if (T == 0) {
+        out1[lane] = -1;
         for (int r = lane; r < FBL2_LEN; r += 32) out[r] = (uint16_t)0xffff;
         return;
     }
@@ -859,6 +864,7 @@ __global__ void k_fbl2(const DevInst *insts, const int2 *rowmap, int words_per_w
             }
             __syncwarp();
         }
+    out1[lane] = lane < T ? (int32_t)(buf[lane] & 0xffffffffu) : -1;
     for (int r = lane; r < FBL2_LEN; r += 32)
         out[r] = r + FBL1_LEN < T ? (uint16_t)(buf[r + FBL1_LEN] & 0xffffu) : (uint16_t)0xffff;
 }
