@@ -320,9 +320,7 @@ int hac_batch_create(const hac_instance *ins, const hac_params *ps, int32_t coun
     int st = plan_batch(ins, ps, count, inputs_on_device, P);
     if (st) return st;
     if (!workspace || ws_bytes < P.total) return HAC_ENOMEM;
-    if (!inputs_on_device)
-        for (int b = 0; b < count; ++b)
-            if ((st = check_host_data(ins[b], ps[b]))) return st;
+    if (!inputs_on_device && (st = check_host_all(ins, ps, count))) return st;
     hac_exec ex;
     hac_exec_default(&ex);
     if (exec) ex = *exec;

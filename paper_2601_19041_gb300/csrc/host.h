@@ -4,6 +4,8 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -108,6 +110,35 @@ inline int check_host_data(const hac_instance &in, const hac_params &p)
     } else {
         for (long long q = 0; q < (long long)n * n; ++q) if (!finite_f(in.cost[q])) return HAC_EINVAL;
     }
+    return HAC_OK;
+}
+
+// check_host_data of every instance of a batch: on up to 16 host threads
+// when the batch holds more than a million heatmap entries and cost-matrix
+// or coordinate values; the status of the first failing instance in batch
+// order (the same as the serial loop)
+inline int check_host_all(const hac_instance *ins, const hac_params *ps, int count)
+{
+    size_t work = 0;
+    for (int b = 0; b < count; ++b)
+        work += (size_t)ins[b].h_nnz + (ins[b].kind == 1 ? (size_t)ins[b].n * ins[b].n : 2 * (size_t)ins[b].n);
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nt = std::min(std::min(hw > 0 ? hw : 1, 16), count);
+    std::vector<int> res(count, HAC_OK);
+    std::atomic<int> next{0};
+    auto worker = [&] {
+        for (int b; (b = next.fetch_add(1)) < count;) res[b] = check_host_data(ins[b], ps[b]);
+    };
+    std::vector<std::thread> th;
+    if (work > (1u << 20))
+        try {
+            for (int t = 1; t < nt; ++t) th.emplace_back(worker);
+        } catch (...) {   // no threads available: the calling thread does the rest
+        }
+    worker();
+    for (std::thread &x : th) x.join();
+    for (int b = 0; b < count; ++b)
+        if (res[b] != HAC_OK) return res[b];
     return HAC_OK;
 }
 

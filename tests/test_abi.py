@@ -96,6 +96,27 @@ def test_host_data_validation_before_cuda(lib):
                                 C.byref(h)) == heataco.HAC_ENOMEM
 
 
+def test_host_data_validation_of_large_batches(lib):
+    """Batches past a million values are validated on several host threads;
+    one malformed instance anywhere still rejects the batch before CUDA."""
+    from paper_2601_19041_gb300 import heataco, synth
+    base = [synth.atsp_instance(700 + b, 200, K=10) for b in range(30)]   # 30 x 200^2 costs
+    p = params(m=4, k=8, iterations=1, rho=0.2, degree_target=1)
+    dummy = C.c_void_p(16)           # never dereferenced: validation fails first
+    for bad_at in (17, 29, 0):
+        insts = list(base)
+        c = insts[bad_at].cost.copy()
+        c[5, 9] = np.inf
+        insts[bad_at] = synth.Instance(n=200, kind=1, coords=None, cost=c, rowptr=insts[bad_at].rowptr,
+                                       col=insts[bad_at].col, val=insts[bad_at].val, symmetrize=0)
+        m = heataco._Marshal(insts, [p] * len(insts), False)
+        ws = C.c_size_t(0)
+        assert lib.hac_batch_workspace_size(m.ins, m.ps, len(insts), 0, C.byref(ws)) == 0
+        h = C.c_void_p()
+        st = lib.hac_batch_create(m.ins, m.ps, len(insts), 0, dummy, ws, None, None, C.byref(h))
+        assert st == heataco.HAC_EINVAL and not h.value
+
+
 def test_server_host_checks_before_cuda(lib):
     from paper_2601_19041_gb300 import heataco
     pts = np.random.default_rng(1).random((60, 2)).astype(np.float32)
