@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--side", type=int, default=-1,
                     help="1: after the batch128 line's own measurement, time the other workloads (tsp500, "
-                         "atsp1000, tsp10k_2opt, serve) in subprocesses and attach their summaries; "
+                         "atsp1000, tsp10k_2opt, serve and the paper settings) in subprocesses and attach "
+                         "their summaries; "
                          "-1 (default): on for the autotuned full batch128 run at N=1")
     ap.add_argument("--cpu-sample", type=int, default=16, help="instances in the CPU sample")
     ap.add_argument("--cpu-iters", type=int, default=20, help="iterations in the CPU sample")
@@ -110,7 +111,7 @@ def dist_env():
 
 
 # DRAM bytes per step of the fused launches measured with ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum of the step's concurrent group
+# (dram__bytes_read.sum + dram__bytes_write.sum of the step's group
 # launches) for a workload and layout; the ncu summary of the default
 # workload under profiles/ gives the command.  Reported as roofline.traffic
 # only for the same workload and layout: the per-instance layout
@@ -357,6 +358,9 @@ SIDE_RUNS = (
     ("tsp10k_2opt", ["--steps", "1", "--warmup", "3", "--no-cpu", "--no-e2e", "--plain-sample", "1",
                      "--autotune", "0", "--fused", "0", "--apw", "1", "--wpb", "8", "--parts", "4"]),
     ("serve", ["--requests", "120", "--warmup", "3"]),
+    ("paper_tsp500", ["--steps", "1", "--warmup", "3", "--no-cpu", "--no-e2e", "--plain-sample", "0"]),
+    ("paper_tsp500_2opt", ["--steps", "1", "--warmup", "3", "--no-cpu", "--no-e2e", "--plain-sample", "0"]),
+    ("paper_tsp1k", ["--steps", "1", "--warmup", "3", "--no-cpu", "--no-e2e", "--plain-sample", "0"]),
 )
 
 
@@ -614,6 +618,7 @@ def run_ours(args):
             walls.append(time.perf_counter() - t0)
         w, = combine_ranks([sum(walls)], "cuda", ["max"])
         e2e = {"value": steps_per * world * args.steps / w, "unit": "ant-steps/s",
+               "ms_per_step": 1000.0 * w / args.steps, "min_ms": 1000.0 * min(walls),
                "h2d_bytes_per_step": input_bytes(insts),
                "d2h_bytes_per_step": int(sum(4 * i.n for i in insts) + 8 * count),
                "instances_per_s": count * world * args.steps / w}

@@ -140,7 +140,7 @@ typedef struct {
                                  coordinates fit in one SM's shared memory, else 2 on a cluster) */
     int32_t warps_per_block;  /* construction block size in warps; 0 = auto */
     int32_t use_graph;        /* 1: capture the iteration loop (per-step kernels: 10 iterations
-                                 per graph; fused: the concurrent group launches) in a CUDA
+                                 per graph; fused: the group launches) in a CUDA
                                  graph, replayed; needs a non-NULL stream */
     int32_t fused;            /* 1: persistent fused construct+update kernel; 0: per-step launches */
     int32_t fallback_list;    /* 32: look up the 32 nearest nodes (key order) before scanning; 0: scan only */
@@ -365,9 +365,8 @@ int hac_server_request_bytes(const hac_instance *in, const hac_params *p, size_t
  * max_slots * 1 KB, the rest is the request heap) and `stream`.  Allocates
  * pinned host staging of about max_slots * (4 * max_n + 512) bytes (and,
  * with step_min_n > 0, per-tick work tables of about max_slots * (16 KB +
- * max_n / 4) bytes, twice, on both sides), one side stream for preparation,
- * three for concurrent cluster-size groups and one for the per-step route,
- * four preparation streams and a pinned upload ring of 64 MB.
+ * max_n / 4) bytes, twice, on both sides), one side stream for the per-step
+ * route, four preparation streams and a pinned upload ring of 64 MB.
  * HAC_ENOMEM if the workspace cannot hold the header and a minimal heap. */
 int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_bytes, void *stream,
                       hac_server **out);

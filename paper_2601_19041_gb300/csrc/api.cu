@@ -231,12 +231,6 @@ static int batch_setup(hac_batch *bt, const hac_instance *ins, const hac_params 
         if (plan_fused(bt, order) == HAC_OK) {
             CK(cudaMemcpyAsync(bt->d_order, order.data(), order.size() * sizeof(int32_t),
                                cudaMemcpyHostToDevice, s));
-            for (size_t g = 1; g < bt->groups.size(); ++g) {
-                FusedGroup &G = bt->groups[g];
-                CK(cudaStreamCreateWithFlags(&G.side, cudaStreamNonBlocking));
-                CK(cudaEventCreateWithFlags(&G.fork, cudaEventDisableTiming));
-                CK(cudaEventCreateWithFlags(&G.join, cudaEventDisableTiming));
-            }
         } else {
             bt->ex.fused = 0;   // some instance does not fit the fused kernel: per-iteration path
             if (bt->ex.ants_per_warp == 0) bt->ex.ants_per_warp = 4;
@@ -404,8 +398,8 @@ static int iterate_part(hac_batch *bt, BatchPart &pt, int todo)
     return HAC_OK;
 }
 
-// the fused groups run concurrently (launch_groups); with CUDA graphs on, the
-// fork/join region of a given iteration count is captured once and replayed
+// the fused groups' launches (launch_groups); with CUDA graphs on, they are
+// captured once per iteration count and replayed
 static int enqueue_fused(hac_batch *bt, int iters)
 {
     if (bt->ex.use_graph && !bt->ex.profile && bt->stream != nullptr) {
@@ -633,11 +627,6 @@ int hac_batch_destroy(hac_batch *bt)
         if (pt.stream && pt.stream != bt->stream) cudaStreamDestroy(pt.stream);
     }
     for (cudaEvent_t e : bt->ev_pool) cudaEventDestroy(e);
-    for (FusedGroup &G : bt->groups) {
-        if (G.side) cudaStreamDestroy(G.side);
-        if (G.fork) cudaEventDestroy(G.fork);
-        if (G.join) cudaEventDestroy(G.join);
-    }
     delete bt;
     return HAC_OK;
 }

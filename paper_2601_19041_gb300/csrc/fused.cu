@@ -56,6 +56,9 @@ __host__ __device__ inline size_t fused_table_bytes(int rows_cap, int kp_cap)
 template <int APW, int NG, int CLOG>
 __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
 {
+    // this CTA is resident: a launch that depends on this one programmatically
+    // (the next layout group) may start once every CTA of this grid is
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int C = 1 << CLOG;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(512, 1) k_fused(FusedArgs A)
 
 template <typename Kern>
 static cudaError_t launch_cluster(Kern kern, int clog, const FusedArgs &A, int clusters, int warps,
-                                  size_t smem, cudaStream_t s)
+                                  size_t smem, cudaStream_t s, bool after_resident)
 {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -223,13 +226,17 @@ static cudaError_t launch_cluster(Kern kern, int clog, const FusedArgs &A, int c
     cfg.blockDim = dim3((unsigned)(warps * 32), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1 << clog;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // after_resident: start as soon as every CTA of the previous launch on the
+    // stream is resident (programmatic dependent launch), not when it ends
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = after_resident ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kern, A);
 }
 
@@ -242,16 +249,16 @@ size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride
 
 cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
                          int clusters, int clog, int apw, int warps, int rows_cap, int kp_cap, int stride,
-                         int xy_cap, int list_rows, int iters, cudaStream_t s)
+                         int xy_cap, int list_rows, int iters, cudaStream_t s, bool after_resident)
 {
     FusedArgs A{d_inst, d_order, d_iters, iters, rows_cap, kp_cap, stride, warps, apw, xy_cap, list_rows};
     const size_t smem = fused_smem_bytes(rows_cap, kp_cap, warps, apw, stride, xy_cap, list_rows);
 #define CLUSTER_SWITCH(APWV, NGV) \
     switch (clog) { \
-    case 0: return launch_cluster(k_fused<APWV, NGV, 0>, 0, A, clusters, warps, smem, s); \
-    case 1: return launch_cluster(k_fused<APWV, NGV, 1>, 1, A, clusters, warps, smem, s); \
-    case 2: return launch_cluster(k_fused<APWV, NGV, 2>, 2, A, clusters, warps, smem, s); \
-    default: return launch_cluster(k_fused<APWV, NGV, 3>, 3, A, clusters, warps, smem, s); }
+    case 0: return launch_cluster(k_fused<APWV, NGV, 0>, 0, A, clusters, warps, smem, s, after_resident); \
+    case 1: return launch_cluster(k_fused<APWV, NGV, 1>, 1, A, clusters, warps, smem, s, after_resident); \
+    case 2: return launch_cluster(k_fused<APWV, NGV, 2>, 2, A, clusters, warps, smem, s, after_resident); \
+    default: return launch_cluster(k_fused<APWV, NGV, 3>, 3, A, clusters, warps, smem, s, after_resident); }
     if (apw == 32) {
         const int G = kp_cap / 4;
         if (G <= 3) { CLUSTER_SWITCH(32, 3) }

@@ -266,7 +266,7 @@ size_t fused_smem_bytes(int rows_cap, int kp_cap, int warps, int apw, int stride
                         int list_rows);
 cudaError_t launch_fused(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
                          int clusters, int clog, int apw, int warps, int rows_cap, int kp_cap, int stride,
-                         int xy_cap, int list_rows, int iters, cudaStream_t s);
+                         int xy_cap, int list_rows, int iters, cudaStream_t s, bool after_resident);
 constexpr size_t FUSED_SMEM_LIMIT = 220 * 1024;   // dynamic shared memory per CTA we allow
 
 }  // namespace hac

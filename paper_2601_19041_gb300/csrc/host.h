@@ -279,8 +279,6 @@ inline int plan_batch(const hac_instance *ins, const hac_params *ps, int count, 
 struct FusedGroup {
     int clog = 0, apw = 4, count = 0, order_off = 0;
     int rows_cap = 0, kp_cap = 0, stride = 0, warps = 0, xy_cap = 0, list_rows = 0;
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // pointers of the zero-initialised part of one instance
@@ -467,28 +465,27 @@ inline int plan_groups(const std::vector<Sizes> &zs, const std::vector<int> &mem
     return HAC_OK;
 }
 
-// Launches the groups concurrently: group 0 on `s`, the others on their side
-// streams, forked from and joined back into `s`.  d_iters (parallel to
-// d_order, may be null) holds per-instance iteration counts.
+// Launches the groups on `s`: group 0 (the batch's longest instances) first,
+// then each further group as a programmatic dependent of the one before it,
+// so that it starts once every CTA of its predecessor is resident rather than
+// when it ends.  Group 0's clusters thus take their SMs before any CTA of a
+// later group can: when the groups' CTAs outnumber the SMs and the launches
+// race (concurrent streams, or a graph's parallel branches), single CTAs may
+// fragment the GPCs so that a 2-CTA cluster of a longest instance finds no
+// free pair of SMs and waits for a small instance to end.  The later groups'
+// surplus CTAs wait in the hardware queue for the SMs that free first.
+// d_iters (parallel to d_order, may be null) holds per-instance iteration
+// counts.
 inline cudaError_t launch_groups(const DevInst *d_inst, const int32_t *d_order, const int32_t *d_iters,
                                  const std::vector<FusedGroup> &groups, int iters, cudaStream_t s)
 {
     cudaError_t err = cudaSuccess;
-    for (size_t g = 1; g < groups.size(); ++g) {
-        cudaEventRecord(groups[g].fork, s);
-        cudaStreamWaitEvent(groups[g].side, groups[g].fork, 0);
-    }
     for (size_t g = 0; g < groups.size(); ++g) {
         const FusedGroup &G = groups[g];
         cudaError_t e = launch_fused(d_inst, d_order + G.order_off, d_iters ? d_iters + G.order_off : nullptr,
                                      G.count, G.clog, G.apw, G.warps,
-                                     G.rows_cap, G.kp_cap, G.stride, G.xy_cap, G.list_rows, iters,
-                                     g ? G.side : s);
+                                     G.rows_cap, G.kp_cap, G.stride, G.xy_cap, G.list_rows, iters, s, g > 0);
         if (e != cudaSuccess && err == cudaSuccess) err = e;
-    }
-    for (size_t g = 1; g < groups.size(); ++g) {
-        cudaEventRecord(groups[g].join, groups[g].side);
-        cudaStreamWaitEvent(s, groups[g].join, 0);
     }
     return err;
 }

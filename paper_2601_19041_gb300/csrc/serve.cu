@@ -116,8 +116,6 @@ struct hac_server {
     char *pinned = nullptr;
     int32_t *h_order[2] = {nullptr, nullptr};   // pinned sources of d_order, then d_iters
     uint64_t next_ticket = 1;
-    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t fork[3] = {nullptr, nullptr, nullptr}, join[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t tick_ev[2] = {nullptr, nullptr};
     // per-step route: stream, fork/join, per-tick compact instance and work tables
     cudaStream_t sstream = nullptr;
@@ -218,12 +216,6 @@ int tick_iters(const hac_server *sv, const Slot &S)
 int enqueue_groups(hac_server *sv, std::vector<FusedGroup> &groups, const int32_t *d_order,
                    const int32_t *d_iters)
 {
-    if (groups.size() > 4) return HAC_EUNSUPPORTED;   // one stream per cluster size
-    for (size_t g = 1; g < groups.size(); ++g) {
-        groups[g].side = sv->side[g - 1];
-        groups[g].fork = sv->fork[g - 1];
-        groups[g].join = sv->join[g - 1];
-    }
     cudaError_t e = launch_groups(sv->d_inst, d_order, d_iters, groups, 0, sv->stream);
     if (e != cudaSuccess) { g_last_cuda = (int)e; return HAC_ECUDA; }
     sv->launches += (long long)groups.size();
@@ -446,11 +438,6 @@ int hac_server_create(const hac_server_cfg *cfg, void *workspace, size_t ws_byte
     for (int g = 0; g < PREP_STREAMS; ++g)
         if ((e = cudaStreamCreateWithFlags(&sv->prep[g], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
     if ((e = cudaHostAlloc((void **)&sv->ring, RING_BYTES, cudaHostAllocDefault)) != cudaSuccess) return fail(e);
-    for (int g = 0; g < 3; ++g) {
-        if ((e = cudaStreamCreateWithFlags(&sv->side[g], cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
-        if ((e = cudaEventCreateWithFlags(&sv->fork[g], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-        if ((e = cudaEventCreateWithFlags(&sv->join[g], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
-    }
     for (int g = 0; g < 2; ++g)
         if ((e = cudaEventCreateWithFlags(&sv->tick_ev[g], cudaEventDisableTiming)) != cudaSuccess) return fail(e);
     // the preparation kernels are the ones that report into the error word
@@ -651,16 +638,10 @@ int hac_server_destroy(hac_server *sv)
 {
     if (!sv) return HAC_EINVAL;
     for (int g = 0; g < PREP_STREAMS; ++g) if (sv->prep[g]) cudaStreamSynchronize(sv->prep[g]);
-    for (int g = 0; g < 3; ++g) if (sv->side[g]) cudaStreamSynchronize(sv->side[g]);
     cudaStreamSynchronize(sv->stream);
     for (Slot &S : sv->slots) {
         if (S.ready) cudaEventDestroy(S.ready);
         if (S.done) cudaEventDestroy(S.done);
-    }
-    for (int g = 0; g < 3; ++g) {
-        if (sv->side[g]) cudaStreamDestroy(sv->side[g]);
-        if (sv->fork[g]) cudaEventDestroy(sv->fork[g]);
-        if (sv->join[g]) cudaEventDestroy(sv->join[g]);
     }
     for (int g = 0; g < 2; ++g) if (sv->tick_ev[g]) cudaEventDestroy(sv->tick_ev[g]);
     if (sv->sstream) { cudaStreamSynchronize(sv->sstream); cudaStreamDestroy(sv->sstream); }
