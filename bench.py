@@ -116,7 +116,7 @@ def dist_env():
 # workload under profiles/ gives the command.  Reported as roofline.traffic
 # only for the same workload and layout: the per-instance layout
 # (ants_per_warp 0) with lookup lists, smallest cluster 1.
-_T_PER_INSTANCE = (0.580602368e9 + 0.929919744e9) + (6.563235072e9 + 3.709806848e9)
+_T_PER_INSTANCE = (0.613120768e9 + 0.943468032e9) + (6.650183680e9 + 3.744521984e9)
 NCU_TRAFFIC = {("batch128", 1, 0, 32, 0, 200): _T_PER_INSTANCE}
 
 
