@@ -367,7 +367,7 @@ SIDE_RUNS = (
 def _side_summary(d):
     """The figures of one workload's line that the default line carries."""
     keep = {k: d.get(k) for k in ("value", "unit", "ms_per_step", "steps", "warmup", "instances_per_s",
-                                  "ant_steps_per_s", "gpu_launches", "device_error")
+                                  "fallback_fraction", "ant_steps_per_s", "gpu_launches", "device_error")
             if d.get(k) is not None}
     cfg = d.get("config", {})
     keep["layout"] = {k: cfg.get(k) for k in ("ants_per_warp", "fused", "cluster_log2", "fallback_list",
@@ -473,6 +473,10 @@ def run_ours(args):
         stats["construct_ms"] += ms0.value
         stats["construct_launches"] += k0.value
         stats["launches"] += nl.value
+        a_s, f_s = C.c_int64(), C.c_int64()     # nearest-unvisited steps (after the timed events)
+        heataco._check(L.hac_batch_counters(h, C.byref(a_s), C.byref(f_s)), "counters")
+        stats["ant_steps"] = stats.get("ant_steps", 0) + a_s.value
+        stats["fallback_steps"] = stats.get("fallback_steps", 0) + f_s.value
         L.hac_batch_destroy(h)
 
     for _ in range(args.warmup):
@@ -651,6 +655,7 @@ def run_ours(args):
                        "fallback_list": args.fbl, "autotune": tune,
                        "kernel_timing": "CUDA events per launch"},
             "instances_per_s": inst_per_s,
+            "fallback_fraction": stats["fallback_steps"] / max(stats["ant_steps"], 1),
             "e2e": e2e,
             "plain_gpu": plain,
             "latency_model": latency,

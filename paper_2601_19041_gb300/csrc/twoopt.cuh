@@ -73,14 +73,18 @@ struct LsMem {
 // Helper warps.  The search is sequential and runs in warp 0; in a block of
 // several warps the others wait at named barrier 1 and take their share of
 // each long segment reversal (its element pairs are independent, so the
-// result does not depend on who swaps which pair).  Protocol, per reversal:
-// warp 0 writes {1, i0, len} to coop, both sides arrive at the barrier, swap
-// their pairs, and arrive again; at the end warp 0 writes {0} and arrives
-// once.  Every path through the search ends with that final arrival.
+// result does not depend on who swaps which pair) and of each wide FP32
+// pre-test of 32 positions (ls_first_may_move, more than 32 work items).
+// Protocol: warp 0 writes a command to coop and every warp arrives at the
+// barrier; then
+//   1 (reverse i0 .. i0+len-1): every warp swaps its pairs, arrives again;
+//   2 (pre-test of the staged cities): the block deals the items 32 * warps
+//     at a time, each round ending at the barrier after the per-warp minima
+//     are written; every thread reads the same minima, so all leave after
+//     the same round (the first with a possible move);
+//   0: the helpers return.
+// Every path through the search ends with command 0.
 constexpr int LS_COOP_LEN = 192;   // reversals of at least this many positions are shared
-// The FP32 pre-test of 32 positions (ls_first_may_move) is shared too when it
-// has more than 32 work items: warp 0 stages its 32 cities and the item counts,
-// and the block deals the items 32 * warps at a time (command 2).
 // coop words: [0] command (0 exit, 1 reverse, 2 pre-test), [1] i0 or item
 // count, [2] len; from LS_ST the staged cities (al, an0, an1, c0, incl, da0,
 // da1; 32 each); from LS_MIN the per-warp minima of two rounds (2 x 8)
