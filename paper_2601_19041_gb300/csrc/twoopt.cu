@@ -8,7 +8,7 @@ namespace hac {
 // One block of LS_WARPS warps per instance: warp 0 runs the search, the other
 // warps help with its long segment reversals and wide pre-tests (twoopt.cuh,
 // 2-opt of symmetric instances) and are released when it ends.
-constexpr int LS_WARPS = 4;   // at most LS_WARPS_MAX
+constexpr int LS_WARPS = 8;   // at most LS_WARPS_MAX
 
 __global__ void k_two_opt_nn(const DevInst *insts, unsigned smem_bytes)
 {
