@@ -82,13 +82,20 @@ struct LsMem {
 //     at a time, each round ending at the barrier after the per-warp minima
 //     are written; every thread reads the same minima, so all leave after
 //     the same round (the first with a possible move);
+//   3 (examine city a): warp 1 searches a's predecessor direction while
+//     warp 0 searches the successor direction (both only read the tour),
+//     writes what it found, and every warp arrives again; warp 0 takes the
+//     successor move if there is one, else warp 1's (the order of the
+//     sequential search);
 //   0: the helpers return.
 // Every path through the search ends with command 0.
 constexpr int LS_COOP_LEN = 192;   // reversals of at least this many positions are shared
-// coop words: [0] command (0 exit, 1 reverse, 2 pre-test), [1] i0 or item
-// count, [2] len; from LS_ST the staged cities (al, an0, an1, c0, incl, da0,
-// da1; 32 each); from LS_MIN the per-warp minima of two rounds (2 x 8)
-constexpr int LS_ST = 8, LS_MIN = LS_ST + 7 * 32, LS_COOP_WORDS = LS_MIN + 16;
+// coop words: [0] command (0 exit, 1 reverse, 2 pre-test, 3 examine), [1] i0,
+// item count or city, [2] len; [3..8] warp 1's predecessor move (found, an, b,
+// bn, d(a,b) and d(an,bn) as FP32 bits); from LS_ST the staged cities (al,
+// an0, an1, c0, incl, da0, da1; 32 each); from LS_MIN the per-warp minima of
+// two rounds (2 x 8)
+constexpr int LS_ST = 10, LS_MIN = LS_ST + 7 * 32, LS_COOP_WORDS = LS_MIN + 16;
 constexpr int LS_WARPS_MAX = 8;
 
 __device__ __forceinline__ void ls_coop_bar(int warps)
@@ -217,6 +224,8 @@ __device__ __forceinline__ int ls_pretest_rounds(const DevInst &I, const LsMem &
     return 32;
 }
 
+__device__ __forceinline__ void ls_pred_search(const DevInst &I, const LsMem &M, int a);
+
 // the helper warps' side of the protocol above (warps 1 .. coop_warps-1)
 __device__ __forceinline__ void ls_coop_help(const DevInst &I, const LsMem &M)
 {
@@ -229,6 +238,9 @@ __device__ __forceinline__ void ls_coop_help(const DevInst &I, const LsMem &M)
             ls_coop_bar(M.coop_warps);
         } else if (cmd == 2) {
             ls_pretest_rounds(I, M, n, I.ls_k, M.coop[1]);
+        } else if (cmd == 3) {
+            if ((threadIdx.x >> 5) == 1) ls_pred_search(I, M, M.coop[1]);
+            ls_coop_bar(M.coop_warps);
         } else {
             break;
         }
@@ -410,6 +422,27 @@ __device__ __forceinline__ bool ls_find_move(const DevInst &I, const LsMem &M, i
     return true;
 }
 
+// Command 3, warp 1: the predecessor direction of city a, written to coop.
+__device__ __forceinline__ void ls_pred_search(const DevInst &I, const LsMem &M, int a)
+{
+    const int lane = threadIdx.x & 31, K = I.ls_k;
+    const int nb = lane < K ? I.nbr[(size_t)a * K + lane] : 0;
+    const float nd32 = lane < K ? I.nbrd32[(size_t)a * K + lane] : 0.0f;
+    const double nd64 = lane < K ? I.nbrd[(size_t)a * K + lane] : 0.0;
+    int an = 0, b = 0, bn = 0;
+    float dab = 0.0f, dn = 0.0f;
+    const bool found = ls_find_move(I, M, I.n, K, a, 1, nb, nd32, nd64, an, b, bn, dab, dn);
+    if (lane == 0) {
+        M.coop[3] = found ? 1 : 0;
+        M.coop[4] = an;
+        M.coop[5] = b;
+        M.coop[6] = bn;
+        M.coop[7] = __float_as_int(dab);
+        M.coop[8] = __float_as_int(dn);
+    }
+    __syncwarp();
+}
+
 // Improves `tour` (global memory) in place.  M holds the working arrays; when
 // M.tour is not `tour`, the tour is copied in and back out.  The array
 // pointers are copied into a local first: the search stores through generic
@@ -465,19 +498,37 @@ static __device__ __noinline__ void warp_two_opt(const DevInst &I, int32_t *tour
                 const double nd64 = lane < K ? I.nbrd[(size_t)a * K + lane] : 0.0;
                 for (;;) {
                     bool moved = false;
-                    for (int dir = 0; dir < 2 && !moved; ++dir) {
-                        int an, b, bn;
-                        float dab, dn;
-                        if (ls_find_move(I, M, n, K, a, dir, nb, nd32, nd64, an, b, bn, dab, dn)) {
-                            if (dir == 0) apply_succ_move(M, n, a, b, dab, dn);
-                            else apply_succ_move(M, n, an, bn, dn, dab);
-                            if (lane == 0) { M.dlb[a] = 0; M.dlb[an] = 0; M.dlb[b] = 0; M.dlb[bn] = 0; }
-                            __syncwarp();
-                            moved = true;
-                            improved = true;
-                            ++round_moves;
-                            ++moves;
+                    int an = 0, b = 0, bn = 0, dir = -1;
+                    float dab = 0.0f, dn = 0.0f;
+                    if (M.coop) {   // both directions at once (command 3), successor first
+                        if (lane == 0) { M.coop[0] = 3; M.coop[1] = a; }
+                        __syncwarp();
+                        ls_coop_bar(M.coop_warps);
+                        const bool f0 = ls_find_move(I, M, n, K, a, 0, nb, nd32, nd64, an, b, bn, dab, dn);
+                        ls_coop_bar(M.coop_warps);
+                        if (f0) {
+                            dir = 0;
+                        } else if (M.coop[3]) {
+                            dir = 1;
+                            an = M.coop[4];
+                            b = M.coop[5];
+                            bn = M.coop[6];
+                            dab = __int_as_float(M.coop[7]);
+                            dn = __int_as_float(M.coop[8]);
                         }
+                    } else {
+                        for (int d = 0; d < 2 && dir < 0; ++d)
+                            if (ls_find_move(I, M, n, K, a, d, nb, nd32, nd64, an, b, bn, dab, dn)) dir = d;
+                    }
+                    if (dir >= 0) {
+                        if (dir == 0) apply_succ_move(M, n, a, b, dab, dn);
+                        else apply_succ_move(M, n, an, bn, dn, dab);
+                        if (lane == 0) { M.dlb[a] = 0; M.dlb[an] = 0; M.dlb[b] = 0; M.dlb[bn] = 0; }
+                        __syncwarp();
+                        moved = true;
+                        improved = true;
+                        ++round_moves;
+                        ++moves;
                     }
                     if (!moved || moves >= max_moves) break;
                 }
